@@ -1,0 +1,67 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle.c (on the CPU, in a
+temporary directory), builds it, swaps it in for the real oracle library and
+runs the pin tests: at least one pin must fail for every mutant, and all of
+them must pass for the unmodified source.
+"""
+import os
+import shutil
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+PIN_CASES = [
+    (pins.test_invariants_tiny, {}),
+    (pins.test_walk_equals_bruteforce_tiny_camera, {}),
+    (pins.test_walk_equals_bruteforce_random_meshes, {"seed": 11}),
+    (pins.test_closed_form_plane, {"direction": 1}),
+    (pins.test_closed_form_plane, {"direction": -1}),
+    (pins.test_closed_form_sphere, {}),
+    (pins.test_restart_rays_equal_bruteforce, {}),
+    (pins.test_locate_contains_point, {}),
+]
+
+MUTANTS = {
+    "face_winding": ("{{1, 3, 2}, {0, 2, 3}, {0, 3, 1}, {0, 1, 2}}",
+                     "{{1, 2, 3}, {0, 2, 3}, {0, 3, 1}, {0, 1, 2}}"),
+    "cross_dropped_term": ("r[2] = a[0] * b[1] - a[1] * b[0];", "r[2] = a[0] * b[1];"),
+    "exit_sign": ("if (nd < 0.0) {", "if (nd > 0.0) {"),
+    "mt_swapped_bary": ("*b1 = dot3(s, p) * inv;", "*b1 = dot3(d, q) * inv; (void)p;"),
+    "tmax_ignored": ("if (tbest > tmax) break;", "(void)tmax;"),
+    "side_flipped": ("m->ctet[2 * c + (s > 0 ? 0 : 1)] = t;", "m->ctet[2 * c + (s > 0 ? 1 : 0)] = t;"),
+    "wrong_neighbour_face": ("kin = m->nbrk[4 * T + best];", "kin = best;"),
+}
+
+
+def run_pins():
+    failed = 0
+    for fn, kw in PIN_CASES:
+        try:
+            fn(**kw)
+        except Exception:  # any pin failure or error counts
+            failed += 1
+    return failed
+
+
+def build_variant(tmp_path, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    return oracle.load(oracle.build(str(path), str(tmp_path / f"lib{name}.so")))
+
+
+def test_unmodified_oracle_passes_pins():
+    assert run_pins() == 0
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, monkeypatch, name):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc missing")
+    lib = build_variant(tmp_path, name, *MUTANTS[name])
+    monkeypatch.setattr(oracle, "_lib", lib)
+    assert run_pins() > 0, f"no pin caught the planted mistake {name}"
