@@ -1,0 +1,470 @@
+#!/usr/bin/env python3
+"""Throughput of constrained tet-mesh ray traversal on one GB300 (or N replicas).
+
+Workload (default, "precision"): 128^3-cell Kuhn grid over [0,1]^3
+(12,582,912 tets, 2,146,689 points, jitter +-0.15 cell), constrained surface
+of 64 seeded random spheres, pinhole camera at (0.5, 0.5, 0.02) looking +z
+with a 70 degree field of view, 2048x2048 primary rays plus one
+cosine-weighted diffuse bounce per hit.  One step = locate the camera tet,
+generate the primary rays, trace them, generate the bounce rays from the
+hits, trace those (all on the device).  Metric: Mrays/s (primary + bounce)
+with the FP32 walk and FP64 guard; the all-FP64 and pure-FP32 arms run the
+same step on the same inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mrays/s (primary + diffuse-bounce) at 1 GB300 vs all-FP64 GPU path; %BW roofline"
+UNIT = "Mrays/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+RAY_BYTES, HIT_BYTES = 32, 32
+# algorithmic bytes: per tet step one Tet16 record + one float4 point; per ray the
+# ray record, the hit record, the start tet's cold record and its four points;
+# per hit the constrained-face record and the triangle's three points.
+STEP_BYTES = 16 + 16
+RAY_FIXED_BYTES = RAY_BYTES + HIT_BYTES + 32 + 4 * 16
+HIT_EXTRA_BYTES = 32 + 3 * 16
+
+WORKLOADS = {
+    "tiny": dict(desc="8^3-cell Kuhn grid (3,072 tets), one sphere, 64x64 primary rays + 1 cosine "
+                      "bounce per hit", per_hit=1, tmax=float("inf"), kind="bounce"),
+    "precision": dict(desc="128^3-cell Kuhn grid (12,582,912 tets, 2,146,689 points, jitter 0.15), "
+                           "64 random spheres, 2048x2048 primary rays + 1 cosine bounce per hit",
+                      per_hit=1, tmax=float("inf"), kind="bounce"),
+    "medium": dict(desc="64^3-cell Kuhn grid (1,572,864 tets), 16 random spheres, 1920x1080 "
+                        "primary rays + 1 cosine bounce per hit",
+                   per_hit=1, tmax=float("inf"), kind="bounce"),
+    "large": dict(desc="256^3-cell Kuhn grid (100,663,296 tets), 256 random spheres, 1024x1024 "
+                       "primary rays + 8 ambient-occlusion rays per hit (t_max 0.05)",
+                  per_hit=8, tmax=0.05, kind="ao"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="precision")
+    p.add_argument("--order", choices=["hilbert", "input"], default="hilbert")
+    p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--refill", type=int, default=0)
+    p.add_argument("--batch-steps", type=int, default=0)
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+            return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("trace.cu", "walk.cuh"):
+        with open(os.path.join(ROOT, "paper_2103_02309_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per trace launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", f"trace_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha")):
+            k, v = line.strip().split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_scene(workload):
+    import scenegen as sg
+    return sg.make_config(workload)
+
+
+# --------------------------------------------------------------------------- #
+# GPU arm
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2103_02309_gb300 import build as libbuild
+    if rank == 0 or not os.path.exists(libbuild.LIB):
+        libbuild.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2103_02309_gb300 import tetmesh as tmx
+
+    W = WORKLOADS[args.workload]
+    s = build_scene(args.workload)
+    t0 = time.time()
+    mesh = tmx.Mesh(s.points, s.tets, s.tris, order=args.order)
+    build_s = time.time() - t0
+    cam = tmx.make_camera(s.camera.eye, s.camera.fov_deg, s.camera.width, s.camera.height)
+    n_primary = s.camera.width * s.camera.height
+    per_hit = W["per_hit"]
+    dev = torch.device("cuda", local)
+    eye = torch.tensor([s.camera.eye], dtype=torch.float32, device=dev)
+    start = torch.empty(1, dtype=torch.int32, device=dev)
+    rays = torch.empty((n_primary, 8), dtype=torch.float32, device=dev)
+    hits = torch.empty((n_primary, 8), dtype=torch.int32, device=dev)
+    rays2 = torch.empty((n_primary * per_hit, 8), dtype=torch.float32, device=dev)
+    hits2 = torch.empty((n_primary * per_hit, 8), dtype=torch.int32, device=dev)
+    count = torch.empty(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def opts(mode):
+        return tmx.trace_opts(mode=mode, block=args.block, refill=args.refill,
+                              batch_steps=args.batch_steps, tmax_early_exit=math.isfinite(W["tmax"]))
+
+    def step(o, ev=None):
+        mesh.locate(eye, out=start)
+        tmx.gen_primary(cam, start, rays=rays)
+        if ev:
+            ev[0].record(stream)
+        mesh.trace(rays, hits=hits, opts=o)
+        if ev:
+            ev[1].record(stream)
+        mesh.gen_secondary(hits, per_hit, W["tmax"], seed=0x5EED, rays_out=rays2, count=count)
+        if ev:
+            ev[2].record(stream)
+        mesh.trace(rays2, hits=hits2, n_dev=count, opts=o)
+        if ev:
+            ev[3].record(stream)
+
+    def timed(mode, steps, warmup):
+        o = opts(mode)
+        for _ in range(warmup):
+            step(o)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = tmx.launch_count()
+        tot, trace_ms = 0.0, 0.0
+        for _ in range(steps):
+            flush.zero_()                                  # evict the mesh from L2 between steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e0.record(stream)
+            step(o, ev)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            trace_ms += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+        torch.cuda.synchronize()
+        launches = tmx.launch_count() - l0
+        if world > 1:
+            torch.distributed.barrier()
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        return tot / steps, trace_ms / steps, launches
+
+    # headline arm: FP32 walk with FP64 guard
+    with ClockSampler(local) as clk:
+        ms, trace_ms, launches = timed("fp32g", args.steps, max(args.warmup, 3))
+    n_second = int(count.item())
+    rays_per_step = n_primary + n_second
+    g1 = tmx.unpack_hits(hits)
+    g2 = tmx.unpack_hits(hits2[:n_second])
+    steps_total = int(g1["steps"].astype(np.int64).sum() + g2["steps"].astype(np.int64).sum())
+    n_hits = int((g1["tri"] >= 0).sum() + (g2["tri"] >= 0).sum())
+    alg_bytes = steps_total * STEP_BYTES + rays_per_step * RAY_FIXED_BYTES + n_hits * HIT_EXTRA_BYTES
+    guard_rate = float(((g1["flags"] & tmx.HIT_GUARD) != 0).mean())
+    final64_rate = float(((np.concatenate([g1["flags"], g2["flags"]]) & tmx.HIT_FINAL_FP64) != 0).mean())
+    value = world * rays_per_step / (ms * 1e-3) / 1e6
+
+    hbm, hbm_src = measured_hbm()
+    achieved = alg_bytes / (trace_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
+                else "fallback 6.8 TB/s",
+                "kernel": "trace_kernel (primary + bounce launches)",
+                "algorithmic_bytes_per_step": alg_bytes,
+                "tet_steps_per_step": steps_total,
+                "trace_share_of_step": round(trace_ms / ms, 4)}
+
+    arms = {}
+    if not args.no_arms:
+        keep = (hits.clone(), hits2.clone(), n_second)
+        for mode in ("fp64", "fp32"):
+            ams, atr, _ = timed(mode, max(2, args.steps // 3), 1)
+            arms[mode] = {"value": round(world * (n_primary + int(count.item())) / (ams * 1e-3) / 1e6, 2),
+                          "ms_per_step": round(ams, 3), "trace_ms": round(atr, 3)}
+            if mode == "fp64":
+                a1 = tmx.unpack_hits(hits)["tri"]
+                arms[mode]["primary_id_agreement_vs_fp32g"] = float((a1 == g1["tri"]).mean())
+        arms["fp32g_speedup_vs_fp64"] = round(value / arms["fp64"]["value"], 2)
+        hits.copy_(keep[0])
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world)
+
+    cpu = None
+    if not args.no_cpu and world == 1 and rank == 0:
+        cpu = cpu_baseline(args.workload, s, W, budget_s=20.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {W['desc']}", "mode": "FP32 walk + FP64 guard",
+                       "tets": s.n_tets, "points": s.n_points, "triangles": s.n_tris,
+                       "rays_per_step": rays_per_step, "primary": n_primary, "secondary": n_second,
+                       "order": args.order, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "flushed between steps (256 MiB write outside the step events)",
+                       "build_s": round(build_s, 2),
+                       "guard_rate_primary": guard_rate, "final_fp64_rate": final64_rate},
+            "roofline": roofline, "arms": arms, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world):
+    """Host rays in, host hits out, through the public API, copies inside the timed region."""
+    start = mesh.locate(torch.tensor([s.camera.eye], dtype=torch.float32, device=dev))
+    rays_dev = tmx.gen_primary(cam, start)
+    rays_host = torch.empty_like(rays_dev, device="cpu").pin_memory()
+    rays_host.copy_(rays_dev)
+    rays_dev2 = torch.empty_like(rays_dev)
+    hits = torch.empty((n_primary, 8), dtype=torch.int32, device=dev)
+    rays2 = torch.empty((n_primary * per_hit, 8), dtype=torch.float32, device=dev)
+    hits2 = torch.empty_like(rays2, dtype=torch.int32)
+    count = torch.empty(1, dtype=torch.int64, device=dev)
+    hits_host = torch.empty(hits.shape, dtype=torch.int32).pin_memory()
+    hits2_host = torch.empty(hits2.shape, dtype=torch.int32).pin_memory()
+    count_host = torch.empty(1, dtype=torch.int64).pin_memory()
+    stream = torch.cuda.current_stream()
+    o = tmx.trace_opts(mode="fp32g", tmax_early_exit=math.isfinite(W["tmax"]))
+
+    def step():
+        rays_dev2.copy_(rays_host, non_blocking=True)
+        mesh.trace(rays_dev2, hits=hits, opts=o)
+        mesh.gen_secondary(hits, per_hit, W["tmax"], seed=0x5EED, rays_out=rays2, count=count)
+        mesh.trace(rays2, hits=hits2, n_dev=count, opts=o)
+        hits_host.copy_(hits, non_blocking=True)
+        hits2_host.copy_(hits2, non_blocking=True)
+        count_host.copy_(count, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 2)
+    tot = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    nr = n_primary + int(count_host.item())
+    return {"value": round(world * nr / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int(rays_host.numel() * 4),
+            "d2h_bytes_per_step": int((hits_host.numel() + hits2_host.numel()) * 4 + 8),
+            "ms_per_step": round(ms, 3)}
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle (baseline leg and reference arm)
+
+
+def oracle_step(om, s, W, cam_tet, sel, nthreads):
+    """One step of the workload on the host oracle for the pixels `sel`; returns rays traced."""
+    import scenegen as sg
+    from oracle.secondary import hit_side, secondary_rays
+    o, d = sg.camera_rays(s.camera)
+    o, d = o[sel], d[sel]
+    w = om.trace(o, d, np.inf, cam_tet, nthreads=nthreads)
+    ctet = om.ctet_cache if hasattr(om, "ctet_cache") else om.arrays()[2]
+    side = hit_side(ctet, w["tri"], w["tet"])
+    o2, d2, tm2, entry, _ = secondary_rays(s.points, s.tris, w["tri"], w["b1"], w["b2"], side,
+                                           0x5EED, W["per_hit"], W["tmax"], ray_ids=sel)
+    om.trace(o2, d2, tm2, -1, entry, nthreads=nthreads)
+    return len(o) + len(o2)
+
+
+def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
+    import oracle
+    nthreads = oracle.default_threads()
+    if om is None:
+        om = oracle.OracleMesh(s.points, s.tets, s.tris)
+    om.ctet_cache = om.arrays()[2]
+    cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
+    n = s.camera.width * s.camera.height
+    stride = 1
+    # size the sample: first a small probe, then as many pixels as fit the budget
+    probe = np.arange(0, n, max(1, n // 20000))
+    t0 = time.time()
+    oracle_step(om, s, W, cam_tet[0], probe, nthreads)
+    rate = len(probe) / max(time.time() - t0, 1e-6)
+    want = int(rate * budget_s)
+    if want < n:
+        stride = max(1, int(math.ceil(n / max(want, 1))))
+    sel = np.arange(0, n, stride)
+    t0 = time.time()
+    traced = oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+    dt = time.time() - t0
+    return {"value": round(traced / dt / 1e6, 4), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"every {stride}th pixel of the {s.camera.width}x{s.camera.height} image "
+                      f"({len(sel)} primary rays) + their {W['kind']} rays; {traced} rays in "
+                      f"{dt:.1f} s (FP64 face-plane walk, numpy secondary-ray generation)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    W = WORKLOADS[args.workload]
+    s = build_scene(args.workload)
+    om = oracle.OracleMesh(s.points, s.tets, s.tris)
+    om.ctet_cache = om.arrays()[2]
+    nthreads = oracle.default_threads()
+    cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
+    n = s.camera.width * s.camera.height
+    stride = 16                                   # a bounded sample: every 16th pixel per step
+    sel = np.arange(0, n, stride)
+    for _ in range(args.warmup):
+        oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+    t0 = time.time()
+    traced = 0
+    for _ in range(args.steps):
+        traced += oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+    dt = time.time() - t0
+    value = traced / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {W['desc']}", "mode": "FP64 oracle walk"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": nthreads,
+                             "kind": "oracle",
+                             "sample": f"every {stride}th pixel ({len(sel)} primary rays) + their "
+                                       f"{W['kind']} rays per step"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

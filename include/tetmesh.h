@@ -1,0 +1,266 @@
+/*
+ * tetmesh.h -- C ABI of the GB300 (sm_103a) library for ray traversal of a
+ * constrained tetrahedral mesh, after Aman, Demirci & Gudukbay, "Compact
+ * Tetrahedralization-based Acceleration Structure for Ray Tracing"
+ * (arXiv 2103.02309).
+ *
+ * The library builds the compact mesh records of Sec. 3 (16-byte Tet16
+ * records, Fig. "Tet16 structure", plus 16-byte aligned float4 points),
+ * orders points and tets along a Hilbert curve (Sec. 5), locates points
+ * with the walk of Sec. 4.2, and traces rays with the 2-D exit-face walk of
+ * Sec. 4 (Alg. 1, Alg. 6-7, the scaled basis of Eq. 1-3 and the projected
+ * origin of Sec. 7, optimisation 1), stopping at the first constrained face
+ * (Sec. 3, last paragraph; Sec. 4, "terminate the traversal").  Secondary
+ * rays restart from a hit face into an adjacent tet (Sec. 6).
+ *
+ * Plain C types only: every pointer is either a host pointer or a CUDA
+ * device pointer, as each function states; streams are cudaStream_t passed
+ * as void*.  Device work is asynchronous on the given stream; the status a
+ * function returns reports argument and launch errors only.  Per-ray
+ * problems are reported in tm_hit.flags.  Functions are thread-safe for
+ * distinct meshes; calls on one mesh from several host threads must be
+ * serialised by the caller.
+ *
+ * Ids: tets and points are renumbered by tm_build (Hilbert order).  Tet ids
+ * that the library returns (tm_hit.tet, tm_locate output) and that it takes
+ * (tm_ray.start >= 0) are INTERNAL ids of that mesh; tm_map_ids converts
+ * them to and from the caller's input ids.  Triangle ids are always the row
+ * of the triangle in the caller's input; each input triangle is one
+ * constrained face, so a constrained-face id equals its triangle id.
+ */
+#ifndef TETMESH_H
+#define TETMESH_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tm_mesh tm_mesh;
+typedef struct tm_batch tm_batch;
+
+typedef enum {
+    TM_OK = 0,
+    TM_ERR_ARG = 1,              /* null pointer, negative count, bad option value */
+    TM_ERR_RANGE = 2,            /* a vertex id outside [0, n_points) */
+    TM_ERR_ORIENT = 3,           /* a tet with orient3d <= 0 (see tm_build) */
+    TM_ERR_NONMANIFOLD = 4,      /* a face shared by more than two tets */
+    TM_ERR_CFACE_UNMATCHED = 5,  /* a triangle that is not a face of any tet */
+    TM_ERR_CFACE_DUPLICATE = 6,  /* two triangles on the same tet face */
+    TM_ERR_OOM = 7,              /* host or device allocation failed */
+    TM_ERR_CUDA = 8,             /* a CUDA call failed; see tm_last_error() */
+    TM_ERR_TOO_LARGE = 9,        /* more than 2^31-1 tets or points, or 2^30 triangles */
+    TM_ERR_NO_DEVICE = 10        /* the mesh was built without upload */
+} tm_status;
+
+/* Arithmetic of the traversal (Sec. 4; the guard is this library's). */
+enum {
+    TM_MODE_FP32_GUARD = 0, /* FP32 walk; a sign test whose |det| < tau*max|coord| is re-decided in FP64 */
+    TM_MODE_FP32 = 1,       /* FP32 walk, no re-test */
+    TM_MODE_FP64 = 2        /* FP64 projections and sign tests throughout */
+};
+
+enum { TM_ORDER_HILBERT = 0, TM_ORDER_INPUT = 1 };
+
+/* A ray, 32 bytes, two 16-byte words.
+ *   start >= 0 : internal id of a tet that holds the origin (o).
+ *   start <  0 : restart from a constrained face (Sec. 6): with
+ *                code = -1 - start, the ray leaves triangle c = code >> 1 into
+ *                the tet on side s = code & 1 of it (0: the side its normal
+ *                (v1-v0) x (v2-v0) points to, in the triangle's input vertex
+ *                order; 1: the other side) and cannot hit c itself.
+ *   tmax       : hits with t > tmax are misses; +inf for unbounded rays.
+ * t is measured in units of |d| (x(t) = o + t d); d need not be unit length. */
+typedef struct {
+    float ox, oy, oz;
+    int32_t start;
+    float dx, dy, dz;
+    float tmax;
+} tm_ray;
+
+/* A hit, 32 bytes.  tri = -1 for a miss.  (b1, b2): barycentrics with
+ * x = (1-b1-b2) v0 + b1 v1 + b2 v2 in the triangle's input vertex order.
+ * tet: internal id of the tet the walk ended in (for a hit, the tet on the
+ * arrival side of the triangle).  steps: tets entered after the start tet. */
+typedef struct {
+    int32_t tri;
+    float t, b1, b2;
+    int32_t tet;
+    int32_t cface;
+    uint32_t steps;
+    uint32_t flags;
+} tm_hit;
+
+#define TM_HIT_SIDE_NEG   0x01u  /* the ray arrived from the - side of the hit triangle */
+#define TM_HIT_STEP_LIMIT 0x02u  /* max_steps reached; reported as a miss */
+#define TM_HIT_GUARD      0x04u  /* at least one sign test was re-decided in FP64 */
+#define TM_HIT_BAD_START  0x08u  /* origin not in the start tet, or an invalid restart face */
+#define TM_HIT_TIE        0x10u  /* an exactly zero sign test was broken by vertex ids */
+#define TM_HIT_FINAL_FP64 0x20u  /* t and barycentrics recomputed in FP64 */
+#define TM_HIT_RESTART_3D 0x40u  /* a restart used the 3-D face-plane fallback step */
+#define TM_HIT_BAD_ID     0x80u  /* an id read from the mesh was out of range (corrupt mesh); miss */
+#define TM_HIT_START_MOVED 0x100u /* the origin lay on the start tet's boundary; the walk started
+                                     in a neighbouring tet that also holds it */
+
+typedef struct {
+    int32_t order;           /* TM_ORDER_HILBERT (default) or TM_ORDER_INPUT */
+    int32_t fix_orientation; /* nonzero: swap V2,V3 of tets with orient3d < 0 instead of failing */
+} tm_build_opts;
+
+typedef struct {
+    int32_t mode;        /* TM_MODE_* */
+    float guard_tau;     /* relative guard threshold; <= 0 selects 1e-6 */
+    uint32_t max_steps;  /* walk bound per ray; 0 selects 4*n_tets^(1/3)*8 + 256 */
+    int32_t block;       /* threads per block: 0 (auto), 64..1024, multiple of 32 */
+    int32_t refill;      /* refill a warp once this many lanes are idle: 0 (auto), 1..32 */
+    int32_t batch_steps; /* walk steps between refill checks: 0 (auto), 1..256 */
+    int32_t ctas_per_sm; /* persistent CTAs per SM: 0 (as many as fit) */
+    int32_t tmax_early_exit; /* nonzero: stop a walk once its entry face lies beyond t_max
+                                (worth it for short rays, e.g. ambient occlusion) */
+} tm_trace_opts;
+
+/* Mesh description returned by tm_mesh_info.  Device pointers are owned by
+ * the mesh and valid until tm_destroy. */
+typedef struct {
+    int64_t n_points, n_tets, n_tris;
+    double extent;               /* largest side of the points' bounding box */
+    float bbox_lo[3], bbox_hi[3];
+    int32_t source_tet;          /* default source tet of tm_locate (internal id) */
+    int32_t on_device;           /* 1 after upload */
+    const void *tet16_dev;       /* int4[n_tets]  (VX, NX0, NX1, NX2) */
+    const void *points_dev;      /* float4[n_points] (x, y, z, 0) */
+    const void *cold_dev;        /* int4[2*n_tets] (V0..V3 positively oriented, N0..N3) */
+    const void *cface_dev;       /* int4[2*n_tris] (tri, tet+, tet-, 0, v0, v1, v2, 0) */
+    int64_t device_bytes;        /* bytes the mesh holds on the device */
+} tm_mesh_info;
+
+/* Builds the compact mesh (Sec. 3) from HOST arrays, which are copied:
+ *   points  float32 [n_points*3] xyz,
+ *   tets    int32 [n_tets*4] vertex ids, positively oriented
+ *           (orient3d(V0,V1,V2,V3) = det[V1-V0, V2-V0, V3-V0] > 0),
+ *   tris    int32 [n_tris*3] vertex ids of the constrained triangles; every
+ *           triangle must be a face of one or two tets.
+ * Steps: face matching (neighbours), constrained-face matching, Hilbert
+ * reordering of points and tet centroids (Sec. 5), Tet16 packing with
+ * neighbours sorted by their opposite vertex id (Sec. 3, Tet20/Tet16), the
+ * cold full records used to start rays, and the constrained-face table
+ * (Sec. 3: a flagged neighbour field indexes it; it keeps the triangle and
+ * both adjacent tets).  upload != 0 also copies the records to the current
+ * CUDA device.  On success *out owns everything; release with tm_destroy.
+ * Errors: TM_ERR_ARG, TM_ERR_RANGE, TM_ERR_ORIENT, TM_ERR_NONMANIFOLD,
+ * TM_ERR_CFACE_UNMATCHED, TM_ERR_CFACE_DUPLICATE, TM_ERR_TOO_LARGE,
+ * TM_ERR_OOM, TM_ERR_CUDA; *out is NULL then. */
+tm_status tm_build(const float *points, int64_t n_points, const int32_t *tets, int64_t n_tets,
+                   const int32_t *tris, int64_t n_tris, const tm_build_opts *opts, int upload,
+                   tm_mesh **out);
+
+/* Releases a mesh and its device arrays (synchronises the device first). */
+void tm_destroy(tm_mesh *mesh);
+
+tm_status tm_mesh_info_get(const tm_mesh *mesh, tm_mesh_info *info);
+
+/* Copies the packed host records into caller HOST buffers (any may be NULL):
+ * tet16 int32[n_tets*4], cold int32[n_tets*8], points float32[n_points*4],
+ * cface int32[n_tris*8], point_perm/tet_perm int32[n] (internal -> input id). */
+tm_status tm_mesh_export(const tm_mesh *mesh, int32_t *tet16, int32_t *cold, float *points,
+                         int32_t *cface, int32_t *point_perm, int32_t *tet_perm);
+
+enum { TM_IDS_TET = 0, TM_IDS_POINT = 1 };
+enum { TM_TO_INPUT = 0, TM_TO_INTERNAL = 1 };
+/* Converts n ids (HOST arrays) between internal and input numbering.  Ids
+ * outside the valid range map to -1. */
+tm_status tm_map_ids(const tm_mesh *mesh, int kind, int direction, const int32_t *in,
+                     int32_t *out, int64_t n);
+
+/* Point location (Sec. 4.2): for each DEVICE point q[i] (float32 xyz,
+ * [n*3]) walks from a source tet's centroid along the segment to q[i] with
+ * the 2-D exit-face test, crossing constrained faces, until the tet whose
+ * exit plane lies beyond q[i]; writes its internal id to tet_out[i] (DEVICE
+ * int32 [n]), or -1 when q[i] is outside the mesh or the walk exceeds its
+ * bound.  hint (DEVICE int32 [n], may be NULL) gives a per-point source tet;
+ * otherwise `source` (an internal id, or -1 for the mesh's default). */
+tm_status tm_locate(const tm_mesh *mesh, const float *q, int64_t n, const int32_t *hint,
+                    int32_t source, int32_t *tet_out, void *stream);
+
+/* Traces n DEVICE rays into n DEVICE hits (Sec. 4 + Sec. 7): one persistent
+ * launch; warps refill idle lanes from a global ray cursor.  If n_dev is not
+ * NULL it points to a DEVICE int64 holding the ray count (read by the
+ * kernel, clamped to n), so that counts produced on the device need no host
+ * round trip.  opts may be NULL (defaults).  rays and hits must be 16-byte
+ * aligned.  Errors: TM_ERR_ARG, TM_ERR_NO_DEVICE, TM_ERR_CUDA. */
+tm_status tm_trace(const tm_mesh *mesh, const tm_ray *rays, int64_t n, const int64_t *n_dev,
+                   tm_hit *hits, const tm_trace_opts *opts, void *stream);
+
+/* Pinhole camera of the synthetic workloads: eye, looking along +z, image x
+ * along +x and image y (down) along -y; per pixel
+ *   sx = ((px+0.5)*kx - 1)*tx,  sy = (1 - (py+0.5)*ky)*ty,
+ *   d = (sx, sy, 1) / sqrt((sx*sx + sy*sy) + 1)   (float64, rounded once),
+ * rays stored in 8x4 pixel tiles, tiles row-major, pixels row-major inside
+ * a tile (ragged edge tiles keep only in-image pixels). */
+typedef struct {
+    float eye[3];
+    int32_t width, height;
+    double kx, ky, tx, ty;  /* kx = 2/W, ky = 2/H, tx,ty = tan(fov/2) * side/shorter side */
+} tm_camera;
+
+/* Writes width*height primary rays (DEVICE tm_ray) starting in the tet
+ * *start_dev (DEVICE int32, e.g. tm_locate's output for the eye). */
+tm_status tm_gen_primary(const tm_camera *cam, const int32_t *start_dev, float tmax,
+                         tm_ray *rays, void *stream);
+
+/* Secondary rays from hits (Sec. 6): for every hit i (tri >= 0) of the n
+ * DEVICE hits, `per_hit` rays leave the hit triangle back into the arrival
+ * side's tet, with cosine-weighted directions about the triangle normal and
+ * the given tmax.  Random numbers: SplitMix64 as a counter-based generator,
+ * draw 2*(i*per_hit + k) + j of stream `seed`.  Output is compacted in hit
+ * order into DEVICE rays_out (capacity n*per_hit), the count is written to
+ * DEVICE *count_dev (int64), and src_out (DEVICE int32, may be NULL) gets the
+ * index i of each ray's hit.  hits may hold n_dev (DEVICE int64, may be
+ * NULL) valid entries instead of n. */
+tm_status tm_gen_secondary(const tm_mesh *mesh, const tm_hit *hits, int64_t n,
+                           const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                           tm_ray *rays_out, int64_t *count_dev, int32_t *src_out, void *stream);
+
+/* Batched, uneven multi-mesh tracing in one persistent launch (a work
+ * queue over all rays of all meshes), replayed from a CUDA graph.
+ * tm_batch_create: meshes (HOST array of n_meshes uploaded meshes).
+ * tm_batch_set: HOST arrays of DEVICE ray/hit pointers and HOST counts; the
+ *   descriptor table is uploaded synchronously and the graph is rebuilt.
+ * tm_batch_run: replays the graph on `stream` (sort + trace).
+ * tm_batch_run_separate: the same work as one tm_trace launch per mesh.
+ * tm_batch_autotune: times candidate (block, refill, batch_steps,
+ *   sort_chunk) settings on the current rays, keeps the fastest, and writes
+ *   it to *best (may be NULL); sort_chunk 0 disables the ray sort. */
+tm_status tm_batch_create(const tm_mesh *const *meshes, int n_meshes, tm_batch **out);
+tm_status tm_batch_set(tm_batch *b, const tm_ray *const *rays, const int64_t *n,
+                       tm_hit *const *hits, const tm_trace_opts *opts, int32_t sort_chunk);
+tm_status tm_batch_run(tm_batch *b, void *stream);
+tm_status tm_batch_run_separate(tm_batch *b, void *stream);
+typedef struct {
+    tm_trace_opts opts;
+    int32_t sort_chunk;
+    float ms;
+} tm_tuned;
+tm_status tm_batch_autotune(tm_batch *b, int reps, tm_tuned *best, void *stream);
+void tm_batch_destroy(tm_batch *b);
+
+/* Host utility: 3-D Hilbert index (Sec. 5's space-filling curve) of n
+ * integer coordinates ijk (HOST uint32 [n*3], each < 2^bits, bits 1..21)
+ * into keys (HOST uint64 [n]).  tm_build orders points and tet centroids by
+ * these keys on a 2^21 grid over the bounding cube. */
+tm_status tm_hilbert_keys(const uint32_t *ijk, int64_t n, int bits, uint64_t *keys);
+
+/* Text of a status; text of the last CUDA error seen by this thread. */
+const char *tm_status_str(tm_status s);
+const char *tm_last_error(void);
+
+/* Number of kernel launches this library has issued in this process (the
+ * benchmark's launch count).  Graph replays count the kernels they hold. */
+uint64_t tm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TETMESH_H */

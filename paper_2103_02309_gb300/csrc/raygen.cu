@@ -1,0 +1,213 @@
+// Ray generation on the device: primary pinhole rays in warp tiles, and
+// secondary rays (diffuse bounce / ambient occlusion) restarted from hit
+// faces into the arrival-side tet (Sec. 6 of the paper), compacted in hit
+// order with a three-pass scan (count per block, scan of the block counts,
+// emit), so the output order does not depend on scheduling.
+#include "tm_internal.h"
+
+namespace tmk {
+
+constexpr int kTileW = 8, kTileH = 4;
+
+__global__ void __launch_bounds__(256)
+gen_primary_kernel(const __grid_constant__ tm_camera cam, const int32_t *__restrict__ start,
+                   float tmax, tm_ray *__restrict__ rays) {
+    const int64_t W = cam.width, H = cam.height, n = W * H;
+    const int32_t st = *start;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        // ray index -> pixel (tile rows of kTileH full rows, the last may be shorter)
+        const int64_t ty = r / (kTileH * W);
+        const int64_t rem = r - ty * kTileH * W;
+        const int64_t th = min((int64_t)kTileH, H - ty * kTileH);
+        const int64_t tx = rem / (kTileW * th);
+        const int64_t rem2 = rem - tx * kTileW * th;
+        const int64_t tw = min((int64_t)kTileW, W - tx * kTileW);
+        const int64_t px = tx * kTileW + rem2 % tw, py = ty * kTileH + rem2 / tw;
+        const double sx = __dmul_rn(__dsub_rn(__dmul_rn(__dadd_rn((double)px, 0.5), cam.kx), 1.0), cam.tx);
+        const double sy = __dmul_rn(__dsub_rn(1.0, __dmul_rn(__dadd_rn((double)py, 0.5), cam.ky)), cam.ty);
+        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), 1.0);
+        const double L = __dsqrt_rn(s2);
+        const float dx = __double2float_rn(__ddiv_rn(sx, L));
+        const float dy = __double2float_rn(__ddiv_rn(sy, L));
+        const float dz = __double2float_rn(__ddiv_rn(1.0, L));
+        float4 *out = reinterpret_cast<float4 *>(rays + r);
+        __stcs(out, make_float4(cam.eye[0], cam.eye[1], cam.eye[2], __int_as_float(st)));
+        __stcs(out + 1, make_float4(dx, dy, dz, tmax));
+    }
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) as a counter-based
+// generator: draw i of stream `seed` is mix64(seed + (i+1) * golden gamma).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ float uniform24(uint64_t seed, uint64_t i) {
+    const uint64_t z = mix64(seed + (i + 1ull) * 0x9E3779B97F4A7C15ull);
+    return (float)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int64_t valid_count(int64_t n, const int64_t *n_dev) {
+    return n_dev ? min(n, *n_dev) : n;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+count_hits_kernel(const tm_hit *__restrict__ hits, int64_t n, const int64_t *n_dev,
+                  int32_t *__restrict__ block_counts) {
+    const int64_t nv = valid_count(n, n_dev);
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    const bool hit = i < nv && __ldg(&hits[i].tri) >= 0;
+    const int c = __syncthreads_count(hit);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = c;
+}
+
+// Exclusive scan of the block counts in one block; total at offsets[nb].
+__global__ void __launch_bounds__(kScanBlock)
+scan_counts_kernel(const int32_t *__restrict__ counts, int64_t nb, int64_t *__restrict__ offsets,
+                   int per_hit, int64_t *__restrict__ count_out) {
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += kScanBlock) {
+        const int64_t i = base + threadIdx.x;
+        int64_t v = i < nb ? counts[i] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        const int64_t before = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
+        if (i < nb) offsets[i] = before;
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        offsets[nb] = carry;
+        *count_out = carry * per_hit;
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
+                      int64_t n, const int64_t *n_dev, const int64_t *__restrict__ offsets,
+                      int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
+                      int32_t *__restrict__ src) {
+    __shared__ int warp_counts[kScanBlock / 32];
+    const int64_t nv = valid_count(n, n_dev);
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    int4 h0 = make_int4(-1, 0, 0, 0), h1 = make_int4(0, 0, 0, 0);
+    if (i < nv) {
+        h0 = __ldcs(reinterpret_cast<const int4 *>(hits + i));
+        h1 = __ldcs(reinterpret_cast<const int4 *>(hits + i) + 1);
+    }
+    const bool hit = h0.x >= 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) warp_counts[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_counts[w];
+    before += __popc(bal & ((1u << lane) - 1u));
+    if (!hit) return;
+    const int64_t pos = offsets[blockIdx.x] + before;
+    const int32_t c = h1.y;
+    const int side = (h1.w & TM_HIT_SIDE_NEG) ? 1 : 0;
+    const int4 cr = __ldg(mv.cface + 2 * c + 1);
+    const float4 a = __ldg(mv.pts + cr.x), b = __ldg(mv.pts + cr.y), d = __ldg(mv.pts + cr.z);
+    const float b1 = __int_as_float(h0.z), b2 = __int_as_float(h0.w);
+    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const float e2x = d.x - a.x, e2y = d.y - a.y, e2z = d.z - a.z;
+    const float ox = a.x + b1 * e1x + b2 * e2x, oy = a.y + b1 * e1y + b2 * e2y,
+                oz = a.z + b1 * e1z + b2 * e2z;
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float inv = rsqrtf(nx * nx + ny * ny + nz * nz) * (side ? -1.f : 1.f);
+    nx *= inv; ny *= inv; nz *= inv;
+    // orthonormal basis around n (Duff et al., JCGT 2017)
+    const float sgn = nz >= 0.f ? 1.f : -1.f;
+    const float aa = -1.f / (sgn + nz), bb = nx * ny * aa;
+    const float t1x = 1.f + sgn * nx * nx * aa, t1y = sgn * bb, t1z = -sgn * nx;
+    const float t2x = bb, t2y = sgn + ny * ny * aa, t2z = -ny;
+    const int32_t start = -1 - (2 * c + side);
+    for (int k = 0; k < per_hit; ++k) {
+        const uint64_t cnt = 2ull * ((uint64_t)i * (uint64_t)per_hit + (uint64_t)k);
+        const float u0 = uniform24(seed, cnt), u1 = uniform24(seed, cnt + 1);
+        float sp, cp;
+        sincospif(2.f * u0, &sp, &cp);
+        const float s = sqrtf(u1), lz = sqrtf(fmaxf(0.f, 1.f - u1));
+        float dx = s * cp * t1x + s * sp * t2x + lz * nx;
+        float dy = s * cp * t1y + s * sp * t2y + lz * ny;
+        float dz = s * cp * t1z + s * sp * t2z + lz * nz;
+        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= il; dy *= il; dz *= il;
+        const int64_t o = pos * per_hit + k;
+        float4 *r = reinterpret_cast<float4 *>(out + o);
+        __stcs(r, make_float4(ox, oy, oz, __int_as_float(start)));
+        __stcs(r + 1, make_float4(dx, dy, dz, tmax));
+        if (src) src[o] = (int32_t)i;
+    }
+}
+
+}  // namespace tmk
+
+tm_status launch_gen_primary(const tm_camera *cam, const int32_t *start, float tmax, tm_ray *rays,
+                             cudaStream_t s) {
+    const int64_t n = (int64_t)cam->width * cam->height;
+    if (n == 0) return TM_OK;
+    int64_t grid = (n + 255) / 256;
+    if (grid > 65535 * 8) grid = 65535 * 8;
+    tmk::gen_primary_kernel<<<(int)grid, 256, 0, s>>>(*cam, start, tmax, rays);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tm_set_error("gen_primary_kernel launch", e);
+        return TM_ERR_CUDA;
+    }
+    tm_count_launches(1);
+    return TM_OK;
+}
+
+tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n,
+                               const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                               tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
+    using tmk::kScanBlock;
+    if (n == 0) {
+        TM_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
+        return TM_OK;
+    }
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb > INT32_MAX) return TM_ERR_TOO_LARGE;
+    int32_t *counts = nullptr;
+    int64_t *offsets = nullptr;
+    TM_CUDA(cudaMallocAsync((void **)&counts, sizeof(int32_t) * nb, s));
+    TM_CUDA(cudaMallocAsync((void **)&offsets, sizeof(int64_t) * (nb + 1), s));
+    tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, counts);
+    tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb, offsets, per_hit, count);
+    tmk::emit_secondary_kernel<<<(int)nb, kScanBlock, 0, s>>>(mv, hits, n, n_dev, offsets, per_hit,
+                                                             tmax, seed, out, src);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(counts, s);
+    cudaFreeAsync(offsets, s);
+    if (e != cudaSuccess) {
+        tm_set_error("gen_secondary launch", e);
+        return TM_ERR_CUDA;
+    }
+    tm_count_launches(3);
+    return TM_OK;
+}

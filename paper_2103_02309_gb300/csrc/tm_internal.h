@@ -1,0 +1,114 @@
+// Internal declarations shared by the host build, the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tetmesh.h"
+
+// A neighbour field holds a tet id (bit 31 clear) or a flagged constrained
+// face (Sec. 3: "a single bitmask ... the remaining 31 bits reference either a
+// neighbouring tetrahedron or a constrained face").  The mesh boundary is the
+// flagged reserved id 0x7FFFFFFF.
+#define TM_CFACE_FLAG 0x80000000u
+#define TM_BOUNDARY 0xFFFFFFFFu
+
+struct tm_mesh {
+    int64_t np = 0, nt = 0, nc = 0;
+    double extent = 0.0;
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int32_t source_tet = 0;
+    // host copies of the packed records
+    std::vector<int32_t> tet16;  // nt*4: VX, NX0, NX1, NX2
+    std::vector<int32_t> cold;   // nt*8: V0..V3 (positive orientation), N0..N3 (N_j across V_j)
+    std::vector<float> pts4;     // np*4
+    std::vector<int32_t> cface;  // nc*8: tri, tet+, tet-, 0, v0, v1, v2, 0
+    std::vector<int32_t> pperm, tperm;  // internal -> input
+    std::vector<int32_t> pinv, tinv;    // input -> internal
+    // device copies
+    int device = -1;
+    bool on_device = false;
+    int4 *d_tet16 = nullptr;
+    float4 *d_pts = nullptr;
+    int4 *d_cold = nullptr;
+    int4 *d_cface = nullptr;
+    int64_t device_bytes = 0;
+};
+
+// What a kernel needs to walk one mesh.
+struct MeshView {
+    const int4 *tet16;
+    const float4 *pts;
+    const int4 *cold;
+    const int4 *cface;
+    int32_t nt, np, nc;
+    float extent;
+};
+
+inline MeshView mesh_view(const tm_mesh *m) {
+    MeshView v;
+    v.tet16 = m->d_tet16;
+    v.pts = m->d_pts;
+    v.cold = m->d_cold;
+    v.cface = m->d_cface;
+    v.nt = (int32_t)m->nt;
+    v.np = (int32_t)m->np;
+    v.nc = (int32_t)m->nc;
+    v.extent = (float)m->extent;
+    return v;
+}
+
+// Error text of the last CUDA failure (thread-local).
+void tm_set_error(const char *what, cudaError_t e);
+void tm_set_error_text(const std::string &s);
+void tm_count_launches(uint64_t n);
+
+#define TM_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t _e = (call);                        \
+        if (_e != cudaSuccess) {                        \
+            tm_set_error(#call, _e);                    \
+            return TM_ERR_CUDA;                         \
+        }                                               \
+    } while (0)
+
+// Kernel launchers (defined in the .cu files).
+struct TraceConfig {
+    int mode;
+    float tau;
+    uint32_t max_steps;
+    int block;
+    int refill;
+    int batch_steps;
+    int ctas_per_sm;
+    bool bounded;
+};
+TraceConfig resolve_trace_opts(const tm_trace_opts *opts, int64_t nt);
+
+tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const int64_t *n_dev,
+                       tm_hit *hits, const TraceConfig &cfg, cudaStream_t s);
+tm_status launch_locate(const MeshView &mv, const float *q, int64_t n, const int32_t *hint,
+                        int32_t source, int32_t *out, uint32_t max_steps, cudaStream_t s);
+tm_status launch_gen_primary(const tm_camera *cam, const int32_t *start, float tmax, tm_ray *rays,
+                             cudaStream_t s);
+tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n,
+                               const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                               tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s);
+
+// Multi-mesh persistent trace over a device descriptor table.
+struct BatchDesc {
+    MeshView mesh;
+    const tm_ray *rays;
+    tm_hit *hits;
+    const int32_t *perm;  // optional ray order (sorted), or null
+    int64_t n;
+    int64_t offset;       // first global ray index of this mesh
+};
+// `count`: add the launch to tm_launch_count (false while capturing a graph).
+tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t total,
+                             const TraceConfig &cfg, unsigned long long *cursor, cudaStream_t s,
+                             bool count);
+int max_persistent_ctas(int mode, bool multi, bool bounded, int block, int *sm_count);

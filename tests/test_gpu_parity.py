@@ -1,0 +1,343 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every input is seeded and synthetic; every expected value comes from the
+oracle.  Tolerances are in tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from oracle.secondary import hit_side, secondary_rays
+from tests.parity import compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def tmx():
+    from paper_2103_02309_gb300 import build
+    build.build()
+    from paper_2103_02309_gb300 import tetmesh
+    return tetmesh
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+class Case:
+    def __init__(self, tmx, scene, order="hilbert"):
+        self.s = scene
+        self.om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
+        self.mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, order=order)
+        e = self.mesh.export()
+        self.tperm = e["tet_perm"]
+        self.tinv = np.empty_like(self.tperm)
+        self.tinv[self.tperm] = np.arange(len(self.tperm))
+        self.nbr, self.fc, self.ctet = self.om.arrays()
+
+    def oracle_trace(self, o, d, tmax, start_input, entry=None):
+        return self.om.trace(o, d, tmax, start_input, entry)
+
+    def gpu_trace(self, tmx, o, d, tmax, start_internal, **kw):
+        rays = dev(tmx.pack_rays(o, d, tmax, start_internal))
+        h = self.mesh.trace(rays, **kw)
+        torch.cuda.synchronize()
+        return tmx.unpack_hits(h)
+
+
+def camera_case(tmx, name, n_override=None, order="hilbert"):
+    s = sg.make_config(name, n_override=n_override)
+    c = Case(tmx, s, order)
+    eye = np.array([s.camera.eye], np.float32)
+    c.cam_in, mb = c.om.locate(eye)
+    assert mb[0] > 1e-9
+    c.cam_internal = int(c.tinv[c.cam_in[0]])
+    return c
+
+
+@pytest.fixture(scope="module")
+def tiny(tmx):
+    return camera_case(tmx, "tiny")
+
+
+def random_case(tmx, n, seed, frac=0.3, jitter=0.2):
+    pts, tets = sg.freudenthal_grid(n, jitter, seed)
+    inside = np.random.default_rng(seed).random((n, n, n)) < frac
+    tris = sg.constrained_faces(n, inside)
+    return Case(tmx, sg.Scene("random", n, jitter, seed, pts, tets, tris, inside))
+
+
+def random_rays(case, count, seed):
+    g = np.random.default_rng(seed)
+    q = g.uniform(0.02, 0.98, size=(count, 3)).astype(np.float32)
+    start, mb = case.om.locate(q)
+    d = g.normal(size=(count, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    keep = mb > 1e-7
+    return q[keep], d[keep], start[keep]
+
+
+# --------------------------------------------------------------------------- #
+
+
+def test_locate_camera_tiny(tmx, tiny):
+    q = dev(np.array([tiny.s.camera.eye], np.float32))
+    t = tiny.mesh.locate(q).cpu().numpy()
+    assert t[0] == tiny.cam_internal
+
+
+@pytest.mark.parametrize("mode", ["fp32g", "fp32", "fp64"])
+def test_tiny_camera_all_rays(tmx, tiny, mode):
+    o, d = sg.camera_rays(tiny.s.camera)
+    w = tiny.oracle_trace(o, d, np.inf, tiny.cam_in[0])
+    g = tiny.gpu_trace(tmx, o, d, np.inf, tiny.cam_internal, mode=mode)
+    st = compare(tiny.s.points, tiny.s.tris, g, w, check_t=(mode != "fp32"))
+    assert st["mismatches"] == 0
+    assert (g["flags"] & (tmx.HIT_BAD_START | tmx.HIT_STEP_LIMIT) == 0).all()
+    # same walk: same number of tets, ends in the same tet, on the same side
+    assert (g["steps"] == w["steps"]).mean() > 0.999
+    hit = w["tri"] >= 0
+    assert np.array_equal(tiny.tperm[g["tet"][hit]], w["tet"][hit])
+    side = hit_side(tiny.ctet, w["tri"], w["tet"])
+    assert np.array_equal((g["flags"][hit] & tmx.HIT_SIDE_NEG) != 0, side[hit] == 1)
+    assert np.array_equal(g["cface"][hit], w["tri"][hit])
+
+
+@pytest.mark.parametrize("w,h", [(64, 64), (37, 13), (8, 4), (1, 1)])
+def test_gen_primary_bit_exact(tmx, tiny, w, h):
+    cam = sg.Camera(tiny.s.camera.eye, 60.0, w, h)
+    o, d = sg.camera_rays(cam)
+    want = tmx.pack_rays(o, d, np.inf, tiny.cam_internal)
+    start = dev(np.array([tiny.cam_internal], np.int32))
+    got = tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, w, h), start).cpu().numpy()
+    assert np.array_equal(got.view(np.int32), want.view(np.int32))
+
+
+@pytest.mark.parametrize("seed", [101, 102, 103])
+@pytest.mark.parametrize("mode", ["fp32g", "fp64", "fp32"])
+def test_random_meshes_random_rays(tmx, seed, mode):
+    c = random_case(tmx, 4 + seed % 3, seed)
+    o, d, start = random_rays(c, 3001, seed)
+    w = c.oracle_trace(o, d, np.inf, start)
+    g = c.gpu_trace(tmx, o, d, np.inf, c.tinv[start], mode=mode)
+    compare(c.s.points, c.s.tris, g, w, check_t=(mode != "fp32"))
+    # bounded rays: hits beyond t_max are misses
+    tm = np.random.default_rng(seed).uniform(0.0, 0.5, len(o)).astype(np.float32)
+    w2 = c.oracle_trace(o, d, tm, start)
+    for early in (False, True):
+        g2 = c.gpu_trace(tmx, o, d, tm, c.tinv[start], mode=mode, tmax_early_exit=early)
+        compare(c.s.points, c.s.tris, g2, w2, check_t=(mode != "fp32"))
+
+
+def test_locate_random_points(tmx):
+    c = random_case(tmx, 6, 77)
+    q = np.random.default_rng(5).uniform(0.0, 1.0, size=(5000, 3)).astype(np.float32)
+    t = c.mesh.locate(dev(q)).cpu().numpy()
+    assert (t >= 0).all()
+    ti = c.tperm[t]
+    worst = min(c.om.tet_bary(ti[i], q[i].astype(np.float64)).min() for i in range(0, len(q), 7))
+    assert worst > -1e-6
+    # a per-point hint gives the same containment
+    hint = dev(np.full(len(q), c.tinv[0], np.int32))
+    t2 = c.mesh.locate(dev(q), hint=hint).cpu().numpy()
+    for i in range(0, len(q), 11):
+        assert c.om.tet_bary(c.tperm[t2[i]], q[i].astype(np.float64)).min() > -1e-6
+    # outside the mesh
+    out = c.mesh.locate(dev(np.array([[1.5, 0.5, 0.5], [-0.1, 0.2, 0.3]], np.float32))).cpu().numpy()
+    assert (out == -1).all()
+
+
+def oracle_secondary(case, w, per_hit, tmax, seed):
+    side = hit_side(case.ctet, w["tri"], w["tet"])
+    return secondary_rays(case.s.points, case.s.tris, w["tri"], w["b1"], w["b2"], side, seed,
+                          per_hit, tmax)
+
+
+@pytest.mark.parametrize("mode", ["fp32g", "fp64"])
+def test_restart_rays(tmx, tiny, mode):
+    cases = [tiny, random_case(tmx, 5, 211, frac=0.35)]
+    for c in cases:
+        if c is tiny:
+            o, d = sg.camera_rays(c.s.camera)
+            start = np.full(len(o), c.cam_in[0], np.int32)
+        else:
+            o, d, start = random_rays(c, 4000, 211)
+        w = c.oracle_trace(o, d, np.inf, start)
+        for per_hit, tmax in ((1, np.inf), (8, 0.05)):
+            o2, d2, tm2, entry, _ = oracle_secondary(c, w, per_hit, tmax, seed=9)
+            w2 = c.oracle_trace(o2, d2, tm2, -1, entry)
+            for early in ((False, True) if np.isfinite(tmax) else (False,)):
+                g2 = c.gpu_trace(tmx, o2, d2, tm2, -1 - entry, mode=mode, tmax_early_exit=early)
+                assert (g2["flags"] & tmx.HIT_BAD_START == 0).all()
+                compare(c.s.points, c.s.tris, g2, w2)
+
+
+def test_gen_secondary_matches_generator(tmx, tiny):
+    o, d = sg.camera_rays(tiny.s.camera)
+    rays = dev(tmx.pack_rays(o, d, np.inf, tiny.cam_internal))
+    hits = tiny.mesh.trace(rays)
+    g = tmx.unpack_hits(hits)
+    side = ((g["flags"] & tmx.HIT_SIDE_NEG) != 0).astype(np.int32)
+    for per_hit, tmax in ((1, np.inf), (8, 0.05)):
+        r2, cnt, src = tiny.mesh.gen_secondary(hits, per_hit, tmax, seed=1234, src=True)
+        torch.cuda.synchronize()
+        k = int(cnt.item())
+        r2 = r2[:k].cpu().numpy()
+        src = src[:k].cpu().numpy()
+        o2, d2, tm2, entry, src_o = secondary_rays(tiny.s.points, tiny.s.tris, g["tri"],
+                                                   g["b1"], g["b2"], side, 1234, per_hit, tmax)
+        assert k == len(o2) == per_hit * (g["tri"] >= 0).sum()
+        assert np.array_equal(src, src_o)
+        assert np.array_equal(r2.view(np.int32)[:, 3], -1 - entry)
+        assert np.abs(r2[:, 0:3] - o2).max() < 1e-6
+        assert np.abs(r2[:, 4:7] - d2).max() < 2e-5
+        assert np.array_equal(r2[:, 7], tm2)
+
+
+def test_hilbert_and_input_order_identical(tmx):
+    s = sg.make_config("medium", n_override=32)
+    a = Case(tmx, s, "hilbert")
+    b = Case(tmx, s, "input")
+    eye = np.array([s.camera.eye], np.float32)
+    cin, _ = a.om.locate(eye)
+    o, d = sg.camera_rays(sg.Camera(s.camera.eye, 70.0, 320, 180))
+    ga = a.gpu_trace(tmx, o, d, np.inf, a.tinv[cin[0]])
+    gb = b.gpu_trace(tmx, o, d, np.inf, b.tinv[cin[0]])
+    tie = ((ga["flags"] | gb["flags"]) & tmx.HIT_TIE) != 0
+    for k in ("tri", "t", "b1", "b2", "steps"):
+        assert np.array_equal(ga[k][~tie], gb[k][~tie]), k
+    assert np.array_equal(a.tperm[ga["tet"]][~tie], b.tperm[gb["tet"]][~tie])
+
+
+@pytest.fixture(scope="module")
+def precision(tmx):
+    """The full-size precision workload (128^3 cells, 2048x2048 camera rays)."""
+    return camera_case(tmx, "precision")
+
+
+@pytest.mark.parametrize("mode", ["fp32g", "fp64", "fp32"])
+def test_precision_full_size_sampled(tmx, precision, mode):
+    c = precision
+    cam = c.s.camera
+    start = dev(np.array([c.cam_internal], np.int32))
+    rays = tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, cam.width, cam.height), start)
+    hits = c.mesh.trace(rays, mode=mode)
+    r2, cnt, src = c.mesh.gen_secondary(hits, 1, np.inf, seed=77, src=True)
+    h2 = c.mesh.trace(r2, n_dev=cnt, mode=mode)
+    torch.cuda.synchronize()
+    n = cam.width * cam.height
+    sel = np.random.default_rng(3).choice(n, 20000, replace=False)
+    o, d = sg.camera_rays(cam)
+    w = c.oracle_trace(o[sel], d[sel], np.inf, c.cam_in[0])
+    g = tmx.unpack_hits(hits[torch.from_numpy(sel).cuda()])
+    st = compare(c.s.points, c.s.tris, g, w, check_t=(mode != "fp32"))
+    # the device-generated bounce rays, sampled, traced by the oracle from the same inputs
+    k = int(cnt.item())
+    sel2 = np.random.default_rng(4).choice(k, min(k, 20000), replace=False)
+    rb = r2[torch.from_numpy(sel2).cuda()].cpu().numpy()
+    code = -1 - rb.view(np.int32)[:, 3]
+    w2 = c.oracle_trace(rb[:, 0:3], rb[:, 4:7], rb[:, 7], -1, code)
+    g2 = tmx.unpack_hits(h2[torch.from_numpy(sel2).cuda()])
+    st2 = compare(c.s.points, c.s.tris, g2, w2, check_t=(mode != "fp32"))
+    print(mode, "primary", st, "bounce", st2)
+
+
+def test_batch_matches_single_launches(tmx):
+    cases = [random_case(tmx, n, 300 + n) for n in (3, 5, 6, 4)]
+    counts = [2500, 0, 1, 7777]
+    rays, want, data = [], [], []
+    for c, cnt in zip(cases, counts):
+        if cnt:
+            o, d, st = random_rays(c, cnt + cnt // 4 + 10, 400 + cnt)
+            o, d, st = o[:cnt], d[:cnt], st[:cnt]
+        else:
+            o = np.zeros((0, 3), np.float32); d = o.copy(); st = np.zeros(0, np.int32)
+        r = dev(tmx.pack_rays(o, d, np.inf, c.tinv[st] if cnt else st))
+        rays.append(r)
+        want.append(tmx.unpack_hits(c.mesh.trace(r)) if cnt else None)
+        data.append((o, d, st))
+    b = tmx.Batch([c.mesh for c in cases])
+    hits = [torch.empty((r.shape[0], 8), dtype=torch.int32, device="cuda") for r in rays]
+    for chunk in (0, 256):
+        for h in hits:
+            h.fill_(-7)
+        b.set(rays, hits, sort_chunk=chunk)
+        b.run()
+        torch.cuda.synchronize()
+        for c, h, wnt, (o, d, st) in zip(cases, hits, want, data):
+            if wnt is None:
+                continue
+            got = tmx.unpack_hits(h)
+            for k in ("tri", "t", "b1", "b2", "tet", "steps"):
+                assert np.array_equal(got[k], wnt[k]), (chunk, k)
+            compare(c.s.points, c.s.tris, got, c.oracle_trace(o, d, np.inf, st))
+    for h in hits:
+        h.fill_(-7)
+    b.run_separate()
+    torch.cuda.synchronize()
+    for h, wnt in zip(hits, want):
+        if wnt is not None:
+            assert np.array_equal(tmx.unpack_hits(h)["tri"], wnt["tri"])
+    t = b.autotune(reps=1)
+    assert t.ms > 0 and t.opts.block in (128, 256, 512)
+    for h in hits:
+        h.fill_(-7)
+    b.run()
+    torch.cuda.synchronize()
+    for h, wnt in zip(hits, want):
+        if wnt is not None:
+            assert np.array_equal(tmx.unpack_hits(h)["tri"], wnt["tri"])
+    b.close()
+
+
+def test_edge_cases(tmx, tiny):
+    m = tiny.mesh
+    # no rays
+    empty = torch.empty((0, 8), dtype=torch.float32, device="cuda")
+    assert m.trace(empty).shape == (0, 8)
+    # invalid starts are flagged, not faulted on
+    o = np.array([[0.5, 0.5, 0.05]] * 4, np.float32)
+    d = np.array([[0, 0, 1]] * 4, np.float32)
+    bad = np.array([tiny.s.n_tets + 5, -1 - 2 * 10 ** 6, tiny.cam_internal, tiny.cam_internal], np.int32)
+    g = tmx.unpack_hits(m.trace(dev(tmx.pack_rays(o, d, np.inf, bad))))
+    assert (g["flags"][:2] & tmx.HIT_BAD_START).all() and (g["tri"][:2] == -1).all()
+    # origin outside the start tet
+    far = tmx.pack_rays(np.array([[0.9, 0.9, 0.9]], np.float32), d[:1], np.inf, tiny.cam_internal)
+    g = tmx.unpack_hits(m.trace(dev(far)))
+    assert g["flags"][0] & tmx.HIT_BAD_START
+    # the step bound ends a walk as a flagged miss
+    o2, d2 = sg.camera_rays(tiny.s.camera)
+    g = tmx.unpack_hits(m.trace(dev(tmx.pack_rays(o2, d2, np.inf, tiny.cam_internal)), max_steps=2))
+    long_walk = g["steps"] >= 2
+    assert long_walk.any() and (g["flags"][long_walk] & tmx.HIT_STEP_LIMIT).all()
+    # a device-side ray count: only the first n_dev rays are traced
+    rays = dev(tmx.pack_rays(o2, d2, np.inf, tiny.cam_internal))
+    hits = torch.full((len(o2), 8), -7, dtype=torch.int32, device="cuda")
+    m.trace(rays, hits=hits, n_dev=torch.tensor([100], dtype=torch.int64, device="cuda"))
+    h = hits.cpu().numpy()
+    assert (h[100:] == -7).all() and (h[:100, 6] != -7).all()
+
+
+def test_axis_aligned_rays_on_unjittered_grid(tmx):
+    """Rays through grid vertices and edges: exact zeros are broken by ids, walks end."""
+    n = 6
+    pts, tets = sg.freudenthal_grid(n, 0.0, 1)
+    tris = sg.constrained_faces(n, sg.slab_cells(n, 4))
+    c = Case(tmx, sg.Scene("slab", n, 0.0, 1, pts, tets, tris, None))
+    g = np.linspace(0.5, 5.5, 6) / n
+    xs, ys = np.meshgrid(g, g)
+    o = np.stack([xs.ravel(), ys.ravel(), np.full(xs.size, 0.3 / n)], 1).astype(np.float32)
+    start, mb = c.om.locate(o)
+    for dvec in ([0, 0, 1], [1, 1, 1], [1, 0, 1], [0.0, 1, 1]):
+        d = np.tile(np.array(dvec, np.float32) / np.linalg.norm(dvec), (len(o), 1)).astype(np.float32)
+        for mode in ("fp32g", "fp32", "fp64"):
+            gh = c.gpu_trace(tmx, o, d, np.inf, c.tinv[start], mode=mode)
+            assert (gh["flags"] & (tmx.HIT_STEP_LIMIT | tmx.HIT_BAD_START) == 0).all()
+            hit = gh["tri"] >= 0
+            # every reported hit lies on the plane z = 4h and on its triangle
+            z0 = np.float32(4 / n)
+            assert np.allclose(o[hit, 2] + gh["t"][hit] * d[hit, 2], z0, atol=1e-6)
