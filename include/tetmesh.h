@@ -194,15 +194,16 @@ tm_status tm_trace(const tm_mesh *mesh, const tm_ray *rays, int64_t n, const int
                    tm_hit *hits, const tm_trace_opts *opts, void *stream);
 
 /* Pinhole camera of the synthetic workloads: eye, looking along +z, image x
- * along +x and image y (down) along -y; per pixel
+ * along +x and image y (down) along -y; per pixel, with correctly rounded
+ * float32 operations in this order (no fused multiply-add):
  *   sx = ((px+0.5)*kx - 1)*tx,  sy = (1 - (py+0.5)*ky)*ty,
- *   d = (sx, sy, 1) / sqrt((sx*sx + sy*sy) + 1)   (float64, rounded once),
+ *   L = sqrt((sx*sx + sy*sy) + 1),  d = (sx/L, sy/L, 1/L),
  * rays stored in 8x4 pixel tiles, tiles row-major, pixels row-major inside
  * a tile (ragged edge tiles keep only in-image pixels). */
 typedef struct {
     float eye[3];
     int32_t width, height;
-    double kx, ky, tx, ty;  /* kx = 2/W, ky = 2/H, tx,ty = tan(fov/2) * side/shorter side */
+    float kx, ky, tx, ty;  /* kx = 2/W, ky = 2/H, tx,ty = tan(fov/2) * side/shorter side */
 } tm_camera;
 
 /* Writes width*height primary rays (DEVICE tm_ray) starting in the tet

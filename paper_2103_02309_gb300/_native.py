@@ -58,8 +58,8 @@ class MeshInfo(ctypes.Structure):
 
 
 class Camera(ctypes.Structure):
-    _fields_ = [("eye", f32 * 3), ("width", i32), ("height", i32), ("kx", f64), ("ky", f64),
-                ("tx", f64), ("ty", f64)]
+    _fields_ = [("eye", f32 * 3), ("width", i32), ("height", i32), ("kx", f32), ("ky", f32),
+                ("tx", f32), ("ty", f32)]
 
 
 class Tuned(ctypes.Structure):

@@ -24,13 +24,11 @@ gen_primary_kernel(const __grid_constant__ tm_camera cam, const int32_t *__restr
         const int64_t rem2 = rem - tx * kTileW * th;
         const int64_t tw = min((int64_t)kTileW, W - tx * kTileW);
         const int64_t px = tx * kTileW + rem2 % tw, py = ty * kTileH + rem2 / tw;
-        const double sx = __dmul_rn(__dsub_rn(__dmul_rn(__dadd_rn((double)px, 0.5), cam.kx), 1.0), cam.tx);
-        const double sy = __dmul_rn(__dsub_rn(1.0, __dmul_rn(__dadd_rn((double)py, 0.5), cam.ky)), cam.ty);
-        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), 1.0);
-        const double L = __dsqrt_rn(s2);
-        const float dx = __double2float_rn(__ddiv_rn(sx, L));
-        const float dy = __double2float_rn(__ddiv_rn(sy, L));
-        const float dz = __double2float_rn(__ddiv_rn(1.0, L));
+        const float sx = __fmul_rn(__fsub_rn(__fmul_rn(__fadd_rn((float)px, 0.5f), cam.kx), 1.0f), cam.tx);
+        const float sy = __fmul_rn(__fsub_rn(1.0f, __fmul_rn(__fadd_rn((float)py, 0.5f), cam.ky)), cam.ty);
+        const float s2 = __fadd_rn(__fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy)), 1.0f);
+        const float L = __fsqrt_rn(s2);
+        const float dx = __fdiv_rn(sx, L), dy = __fdiv_rn(sy, L), dz = __fdiv_rn(1.0f, L);
         float4 *out = reinterpret_cast<float4 *>(rays + r);
         __stcs(out, make_float4(cam.eye[0], cam.eye[1], cam.eye[2], __int_as_float(st)));
         __stcs(out + 1, make_float4(dx, dy, dz, tmax));
@@ -211,3 +209,4 @@ tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n
     tm_count_launches(3);
     return TM_OK;
 }
+

@@ -9,7 +9,8 @@
 //   idx3 = idx0 ^ idx1 ^ idx2 ^ VX
 //   ra = rank of idx3, rb = rank of idx_exit among the four vertex ids
 //   N3 = ra == 3 ? prev : prev ^ NX_ra ;  next = rb == 3 ? N3 : N3 ^ NX_rb
-// and stops at a flagged (constrained or boundary) neighbour.
+// and stops at a flagged (constrained or boundary) neighbour.  Alg. 1 is
+// evaluated from the three signs det(p3, p_k) without branches.
 //
 // Warps are persistent: lanes whose ray ended are refilled from a global
 // cursor once `refill` lanes are idle (ballot + popc, one atomicAdd per
@@ -23,12 +24,6 @@
 
 namespace tmk {
 
-// Register budget of the FP32 walk: at least this many 512-thread blocks
-// per SM (3 -> at most 40 registers per thread).
-#ifndef TM_TRACE_MIN_BLOCKS
-#define TM_TRACE_MIN_BLOCKS 3
-#endif
-
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBatch = 64;
 
@@ -37,69 +32,29 @@ struct TraceParams {
     const int64_t *n_dev;
     unsigned long long *cursor;
     uint32_t max_steps;
-    float tau_rel;   // sign-test guard threshold relative to the mesh extent
+    float tau_rel;  // sign-test guard threshold relative to the mesh extent
     int refill;
     int batch_steps;
 };
 
-// Final hit in double precision (guard path, out of line).
-__device__ __noinline__ static void mt_hit_fp64(const float4 o4, const float4 d4, const float4 a4,
-                                                const float4 b4, const float4 c4, float *t,
-                                                float *b1, float *b2) {
-    double td, u, v, cs;
-    mt_hit<double>(o4, d4, a4, b4, c4, td, u, v, cs);
-    *t = (float)td;
-    *b1 = (float)u;
-    *b2 = (float)v;
+// Final hit in double precision: (t, b1, b2).  Out of line: the guard path.
+__device__ __noinline__ static float4 mt_hit_fp64(const float4 o4, const float4 d4, const float4 a4,
+                                                  const float4 b4, const float4 c4) {
+    double t, u, v, cond;
+    mt_hit<double>(o4, d4, a4, b4, c4, t, u, v, cond);
+    return make_float4((float)t, (float)u, (float)v, 0.f);
 }
 
-// Rare start fallback: the origin lies on the boundary of the start tet and
-// the line (with ties broken by vertex ids) does not pass through it.  Try
-// the tets around it, up to two rings of face neighbours, that also hold the
-// origin, and start in the one the line leaves through.
-template <int MODE, class R>
-__device__ __noinline__ bool search_start(const MeshView &mv, const Basis<R> &B, const tm_ray *rp,
-                                          int32_t T0, SignCtx &sc, WalkState<R> &S,
-                                          uint32_t &next) {
-    int32_t tried[21];
-    int nt = 0;
-    tried[nt++] = T0;
-    int32_t ring[4];
-    const int4 n0 = __ldg(mv.cold + 2 * T0 + 1);
-    ring[0] = n0.x; ring[1] = n0.y; ring[2] = n0.z; ring[3] = n0.w;
-    for (int level = 0; level < 2; ++level) {
-        int32_t cand[16];
-        int nc = 0;
-        if (level == 0) {
-            for (int k = 0; k < 4; ++k) cand[nc++] = ring[k];
-        } else {
-            for (int k = 0; k < 4; ++k) {
-                if (ring[k] < 0 || ring[k] >= mv.nt) continue;
-                const int4 nn = __ldg(mv.cold + 2 * ring[k] + 1);
-                const int32_t q[4] = {nn.x, nn.y, nn.z, nn.w};
-                for (int j = 0; j < 4; ++j) cand[nc++] = q[j];
-            }
-        }
-        for (int i = 0; i < nc; ++i) {
-            const int32_t c = cand[i];
-            if (c < 0 || c >= mv.nt) continue;  // flagged (constrained / boundary) or invalid
-            bool seen = false;
-            for (int j = 0; j < nt; ++j) seen |= tried[j] == c;
-            if (seen || nt >= 21) continue;
-            tried[nt++] = c;
-            if (!holds_origin(mv, rp, c)) continue;
-            if (line_init<MODE>(mv, B, c, -1, sc, S, next)) return true;
-        }
-    }
-    return false;
-}
+// In guard mode the float32 ray-triangle test is redone in double precision
+// when its condition estimate (see mt_hit) exceeds kFinalCond, i.e. when the
+// float32 t could be off by more than about 2e-6 relative.
+constexpr float kFinalCond = 32.f;
 
 // Writes the hit (or miss) of a finished ray.  `code` is the flagged
 // neighbour value that ended the walk in tet `tet`.
 template <int MODE>
 __device__ __forceinline__ void finish(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
-                                       uint32_t code, int32_t tet, uint32_t steps, uint32_t flags,
-                                       float t_final) {
+                                       uint32_t code, int32_t tet, uint32_t steps, uint32_t flags) {
     const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
     const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
     int32_t tri = -1, cf = -1;
@@ -111,16 +66,18 @@ __device__ __forceinline__ void finish(const MeshView &mv, const tm_ray *rp, tm_
     if (code != TM_BOUNDARY) {
         const int32_t c = (int32_t)(code & ~TM_CFACE_FLAG);
         const int4 r0 = __ldg(mv.cface + 2 * c);
-        const int4 r1 = __ldg(mv.cface + 2 * c + 1);
+        const int4 r1 = __ldg(mv.cface + 2 * c + 1);  // vertex ids validated by the host build
         const float4 a = __ldg(mv.pts + r1.x), b = __ldg(mv.pts + r1.y), d = __ldg(mv.pts + r1.z);
-        float th, u, v;  // (face-table vertex ids are validated by the host build)
+        float th, u, v;
         if (MODE == FP64) {
-            mt_hit_fp64(w0, w1, a, b, d, &th, &u, &v);
+            const float4 h = mt_hit_fp64(w0, w1, a, b, d);
+            th = h.x; u = h.y; v = h.z;
         } else {
-            float cs;
-            mt_hit<float>(w0, w1, a, b, d, th, u, v, cs);
-            if (MODE == FP32G && (!(th >= t_final) || !(cs >= 1e-3f))) {
-                mt_hit_fp64(w0, w1, a, b, d, &th, &u, &v);
+            float cond;
+            mt_hit<float>(w0, w1, a, b, d, th, u, v, cond);
+            if (MODE == FP32G && !(cond <= kFinalCond)) {
+                const float4 h = mt_hit_fp64(w0, w1, a, b, d);
+                th = h.x; u = h.y; v = h.z;
                 flags |= TM_HIT_FINAL_FP64;
             }
         }
@@ -136,6 +93,71 @@ __device__ __forceinline__ void finish(const MeshView &mv, const tm_ray *rp, tm_
     __stcs(reinterpret_cast<int4 *>(hp), make_int4(tri, __float_as_int(t), __float_as_int(b1),
                                                    __float_as_int(b2)));
     __stcs(reinterpret_cast<int4 *>(hp) + 1, make_int4(tet, cf, (int)steps, (int)flags));
+}
+
+// Once per ray and with only value arguments: out of line by default.
+#ifdef TM_FINISH_INLINE
+#define TM_FINISH_ATTR __forceinline__
+#else
+#define TM_FINISH_ATTR __noinline__
+#endif
+
+template <int MODE>
+__device__ TM_FINISH_ATTR void finish_ray(const MeshView mv, const tm_ray *rp, tm_hit *hp,
+                                          uint32_t code, int32_t tet, uint32_t steps,
+                                          uint32_t flags) {
+    finish<MODE>(mv, rp, hp, code, tet, steps, flags);
+}
+
+// Rare start fallback: the origin lies on the boundary of the start tet and
+// the line (with ties broken by vertex ids) does not pass through it.  Among
+// the tets around it, up to two rings of face neighbours, returns the first
+// that also holds the origin and that the line leaves through exactly one
+// face; -1 if none.
+template <int MODE>
+__device__ __noinline__ int32_t search_start(const MeshView mv, const tm_ray *rp, int32_t T0,
+                                             float tau) {
+    typedef typename RealOf<MODE>::T R;
+    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
+    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
+    const Basis<R> B = make_basis<R>(R(w1.x), R(w1.y), R(w1.z), R(w0.x), R(w0.y), R(w0.z));
+    SignCtx sc;
+    sc.ray = rp;
+    sc.pts = mv.pts;
+    sc.tau = tau;
+    sc.flags = 0;
+    int32_t tried[21];
+    int n_tried = 0;
+    tried[n_tried++] = T0;
+    int32_t ring[4];
+    const int4 n0 = __ldg(mv.cold + 2 * T0 + 1);
+    ring[0] = n0.x; ring[1] = n0.y; ring[2] = n0.z; ring[3] = n0.w;
+    for (int level = 0; level < 2; ++level) {
+        int32_t cand[16];
+        int nc = 0;
+        if (level == 0) {
+            for (int k = 0; k < 4; ++k) cand[nc++] = ring[k];
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                if (ring[k] < 0 || ring[k] >= mv.nt) continue;
+                const int4 nn = __ldg(mv.cold + 2 * ring[k] + 1);
+                cand[nc++] = nn.x; cand[nc++] = nn.y; cand[nc++] = nn.z; cand[nc++] = nn.w;
+            }
+        }
+        for (int i = 0; i < nc; ++i) {
+            const int32_t c = cand[i];
+            if (c < 0 || c >= mv.nt) continue;  // flagged (constrained / boundary) or invalid
+            bool seen = false;
+            for (int j = 0; j < n_tried; ++j) seen |= tried[j] == c;
+            if (seen || n_tried >= 21) continue;
+            tried[n_tried++] = c;
+            if (!holds_origin(mv, rp, c)) continue;
+            WalkState<R> S;
+            uint32_t next;
+            if (line_init<MODE>(mv, B, c, -1, sc, S, next)) return c;
+        }
+    }
+    return -1;
 }
 
 template <class R, bool BOUNDED> struct Depth {
@@ -161,8 +183,103 @@ template <class R> struct Depth<R, true> {
     __device__ __forceinline__ bool beyond() const { return fmin(z0, fmin(z1, z2)) > zmax; }
 };
 
+// Starts the ray at rp: basis, projected origin, and the exit face of its
+// start tet (interior start) or of the tet behind its restart face.  Returns
+// true when the walk continues in S.tet; otherwise the hit is written.
+template <int MODE, bool BOUNDED>
+__device__ __forceinline__ bool start_ray(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
+                                          WalkState<typename RealOf<MODE>::T> &S,
+                                          Basis<typename RealOf<MODE>::T> &B,
+                                          Depth<typename RealOf<MODE>::T, BOUNDED> &Z,
+                                          SignCtx &sc, uint32_t &steps) {
+    typedef typename RealOf<MODE>::T R;
+    const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(rp));
+    const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(rp) + 1);
+    B = make_basis<R>(R(w1.x), R(w1.y), R(w1.z), R(w0.x), R(w0.y), R(w0.z));
+    sc.flags = 0;
+    steps = 0;
+    const int32_t start = __float_as_int(w0.w);
+    uint32_t next = TM_BOUNDARY;
+    int32_t T = -1;
+    bool ok = false;
+    if (start >= 0) {
+        if (start < mv.nt) {
+            T = start;
+            ok = line_init<MODE>(mv, B, T, -1, sc, S, next);
+            if (!ok) {
+                const int32_t T2 = search_start<MODE>(mv, rp, T, sc.tau);
+                if (T2 >= 0) {
+                    T = T2;
+                    ok = line_init<MODE>(mv, B, T, -1, sc, S, next);
+                    sc.flags |= TM_HIT_START_MOVED;
+                }
+            }
+        }
+    } else {
+        const int32_t code = -1 - start;
+        const int32_t c = code >> 1;
+        if (c < mv.nc) {
+            const int4 r0 = __ldg(mv.cface + 2 * c);
+            T = (code & 1) ? r0.z : r0.y;
+        }
+        if (T >= mv.nt) T = -1;
+        if (T >= 0) {
+            const int4 cn = __ldg(mv.cold + 2 * T + 1);
+            const uint32_t want = TM_CFACE_FLAG | (uint32_t)c;
+            int skip = (uint32_t)cn.x == want ? 0 : (uint32_t)cn.y == want ? 1
+                     : (uint32_t)cn.z == want ? 2 : (uint32_t)cn.w == want ? 3 : -1;
+            if (skip >= 0) {
+                ok = line_init<MODE>(mv, B, T, skip, sc, S, next);
+                for (int it = 0; !ok && it < 16; ++it) {
+                    // the line misses T by rounding: one 3-D step, then retry
+                    sc.flags |= TM_HIT_RESTART_3D;
+                    const int2 st = step3d(mv, rp, T, skip);
+                    const uint32_t nb = (uint32_t)st.x;
+                    if (nb & TM_CFACE_FLAG) { next = nb; S.prev = T; ok = true; break; }
+                    if (nb >= (uint32_t)mv.nt || st.y < 0) break;
+                    ++steps;
+                    T = (int32_t)nb;
+                    skip = st.y;
+                    ok = line_init<MODE>(mv, B, T, skip, sc, S, next);
+                }
+            } else {
+                T = -1;
+            }
+        }
+    }
+    if (!ok) {
+        finish_ray<MODE>(mv, rp, hp, TM_BOUNDARY, T, steps, sc.flags | TM_HIT_BAD_START);
+        return false;
+    }
+    if (next & TM_CFACE_FLAG) {
+        finish_ray<MODE>(mv, rp, hp, next, S.prev, steps, sc.flags);
+        return false;
+    }
+    S.tet = (int32_t)next;
+    if (BOUNDED) {
+        Z.init(R(w0.x), R(w0.y), R(w0.z), R(w1.x), R(w1.y), R(w1.z), w1.w);
+        Z.set(0, __ldg(mv.pts + S.i0));
+        Z.set(1, __ldg(mv.pts + S.i1));
+        Z.set(2, __ldg(mv.pts + S.i2));
+        if (Z.beyond()) {
+            finish_ray<MODE>(mv, rp, hp, TM_BOUNDARY, S.prev, steps, sc.flags);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Register budget per thread of the walk (FP32 arms; the FP64 arm needs
+// double-width state).  Set by measurement on GB300.
+#ifndef TM_TRACE_MAXREG
+#define TM_TRACE_MAXREG 64
+#endif
+#ifndef TM_TRACE_MAXREG_FP64
+#define TM_TRACE_MAXREG_FP64 80
+#endif
+
 template <int MODE, bool BOUNDED, bool MULTI>
-__global__ void __launch_bounds__(512, MODE == FP64 ? 2 : TM_TRACE_MIN_BLOCKS)
+__global__ void __maxnreg__(MODE == FP64 ? TM_TRACE_MAXREG_FP64 : TM_TRACE_MAXREG)
 trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
              tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
              const __grid_constant__ TraceParams P) {
@@ -173,7 +290,6 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     int64_t n = P.n_cap;
     if (P.n_dev) n = min(n, *P.n_dev);
 
@@ -181,12 +297,14 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
     int32_t m = 0, local = 0;
     const int4 *tet16 = mv0.tet16;
     const float4 *pts = mv0.pts;
-    const tm_ray *rp = nullptr;
     WalkState<R> S;
     Basis<R> B;
     Depth<R, BOUNDED> Z;
     SignCtx sc;
-    sc.tau = 0.f;
+    sc.ray = nullptr;
+    sc.pts = pts;
+    sc.tau = P.tau_rel * mv0.extent;
+    sc.flags = 0;
     uint32_t steps = 0;
 
     for (;;) {
@@ -197,7 +315,7 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
             if (lane == 0) base = atomicAdd(P.cursor, (unsigned long long)n_idle);
             base = __shfl_sync(kFull, base, 0);
             if (base + (unsigned long long)n_idle >= (unsigned long long)n) pool_empty = true;
-            const unsigned long long r = base + __popc(idle & lt_mask);
+            const unsigned long long r = base + __popc(idle & ((1u << lane) - 1u));
             if (!active && r < (unsigned long long)n) {
                 tm_hit *hp;
                 if (MULTI) {
@@ -211,86 +329,17 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
                     if (sdesc[m].perm) local = sdesc[m].perm[local];
                     tet16 = sdesc[m].mesh.tet16;
                     pts = sdesc[m].mesh.pts;
-                    rp = sdesc[m].rays + local;
+                    sc.ray = sdesc[m].rays + local;
+                    sc.pts = pts;
+                    sc.tau = P.tau_rel * sdesc[m].mesh.extent;
                     hp = sdesc[m].hits + local;
                 } else {
                     local = (int32_t)r;
-                    rp = rays0 + local;
+                    sc.ray = rays0 + local;
                     hp = hits0 + local;
                 }
-                const MeshView &mv = MULTI ? sdesc[m].mesh : mv0;
-                const float t_final = mv.extent * (1.0f / 64.0f);
-                const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(rp));
-                const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(rp) + 1);
-                B = make_basis<R>(R(w1.x), R(w1.y), R(w1.z), R(w0.x), R(w0.y), R(w0.z));
-                sc.ray = rp;
-                sc.pts = pts;
-                sc.tau = P.tau_rel * mv.extent;
-                sc.flags = 0;
-                steps = 0;
-                const int32_t start = __float_as_int(w0.w);
-                uint32_t next = TM_BOUNDARY;
-                int32_t T = -1;
-                bool ok = false;
-                if (start >= 0) {
-                    if (start < mv.nt) {
-                        T = start;
-                        ok = line_init<MODE>(mv, B, T, -1, sc, S, next);
-                        if (!ok) {
-                            ok = search_start<MODE>(mv, B, rp, T, sc, S, next);
-                            if (ok) sc.flags |= TM_HIT_START_MOVED;
-                        }
-                    }
-                } else {
-                    const int32_t code = -1 - start;
-                    const int32_t c = code >> 1;
-                    if (c < mv.nc) {
-                        const int4 r0 = __ldg(mv.cface + 2 * c);
-                        T = (code & 1) ? r0.z : r0.y;
-                    }
-                    if (T >= mv.nt) T = -1;
-                    if (T >= 0) {
-                        const int4 cn = __ldg(mv.cold + 2 * T + 1);
-                        const uint32_t want = TM_CFACE_FLAG | (uint32_t)c;
-                        int skip = (uint32_t)cn.x == want ? 0 : (uint32_t)cn.y == want ? 1
-                                 : (uint32_t)cn.z == want ? 2 : (uint32_t)cn.w == want ? 3 : -1;
-                        if (skip >= 0) {
-                            ok = line_init<MODE>(mv, B, T, skip, sc, S, next);
-                            for (int it = 0; !ok && it < 16; ++it) {
-                                // the line misses T by rounding: one 3-D step, then retry
-                                sc.flags |= TM_HIT_RESTART_3D;
-                                int skip_next;
-                                const uint32_t nb = step3d(mv, rp, T, skip, &skip_next);
-                                if (nb & TM_CFACE_FLAG) { next = nb; S.prev = T; ok = true; break; }
-                                if (nb >= (uint32_t)mv.nt || skip_next < 0) break;
-                                ++steps;
-                                T = (int32_t)nb;
-                                skip = skip_next;
-                                ok = line_init<MODE>(mv, B, T, skip, sc, S, next);
-                            }
-                        } else {
-                            T = -1;
-                        }
-                    }
-                }
-                if (!ok) {
-                    finish<MODE>(mv, rp, hp, TM_BOUNDARY, T, steps, sc.flags | TM_HIT_BAD_START,
-                                 t_final);
-                } else if (next & TM_CFACE_FLAG) {
-                    finish<MODE>(mv, rp, hp, next, S.prev, steps, sc.flags, t_final);
-                } else {
-                    S.tet = (int32_t)next;
-                    if (BOUNDED) {
-                        Z.init(R(w0.x), R(w0.y), R(w0.z), R(w1.x), R(w1.y), R(w1.z), w1.w);
-                        Z.set(0, __ldg(pts + S.i0));
-                        Z.set(1, __ldg(pts + S.i1));
-                        Z.set(2, __ldg(pts + S.i2));
-                    }
-                    if (BOUNDED && Z.beyond())
-                        finish<MODE>(mv, rp, hp, TM_BOUNDARY, S.prev, steps, sc.flags, t_final);
-                    else
-                        active = true;
-                }
+                active = start_ray<MODE, BOUNDED>(MULTI ? sdesc[m].mesh : mv0, sc.ray, hp, S, B, Z,
+                                                  sc, steps);
             }
         }
         if (!__any_sync(kFull, active)) {
@@ -298,40 +347,36 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
             continue;
         }
         for (int k = 0; k < P.batch_steps; ++k) {
-            if (active) {
-                // ---- one step of Alg. 6 / Alg. 7 ----
-                const int4 rec = __ldg(tet16 + S.tet);
-                const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.x;
-                const int32_t np_ = MULTI ? sdesc[m].mesh.np : mv0.np;
-                if ((uint32_t)i3 >= (uint32_t)np_) {
-                    // a corrupt record: end the ray instead of reading out of bounds
-                    const MeshView &mv = MULTI ? sdesc[m].mesh : mv0;
-                    tm_hit *hp = MULTI ? sdesc[m].hits + local : hits0 + local;
-                    finish<MODE>(mv, rp, hp, TM_BOUNDARY, S.tet, steps, sc.flags | TM_HIT_BAD_ID,
-                                 mv.extent * (1.0f / 64.0f));
-                    active = false;
-                    continue;
-                }
+            if (!active) continue;
+            // ---- one step of Alg. 6 / Alg. 7 ----
+            const int4 rec = __ldg(tet16 + S.tet);
+            const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.x;
+            uint32_t code = TM_BOUNDARY;
+            bool done = false;
+            if ((uint32_t)i3 >= (uint32_t)(MULTI ? sdesc[m].mesh.np : mv0.np)) {
+                // a corrupt record: end the ray instead of reading out of bounds
+                done = true;
+                sc.flags |= TM_HIT_BAD_ID;
+            } else {
                 const float4 x = __ldg(pts + i3);
                 const P2<R> p3 = B.project(R(x.x), R(x.y), R(x.z));
-                const int e = exit_slot<MODE>(S.p0, S.p1, S.p2, p3, S.i0, S.i1, S.i2, i3, sc);
+                const float m3 = MODE == FP32G ? guard_mag(p3, sc.tau) : 0.f;
+                const int e = exit_slot_bits(step_signs<MODE>(S, p3, i3, m3, sc));
                 const int ra = (S.i0 < i3) + (S.i1 < i3) + (S.i2 < i3);
                 const int32_t ie = e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2);
                 const int rb = (S.i0 < ie) + (S.i1 < ie) + (S.i2 < ie) + (i3 < ie);
                 const uint32_t nxa = ra == 0 ? rec.y : (ra == 1 ? rec.z : (ra == 2 ? rec.w : 0));
                 const uint32_t nxb = rb == 0 ? rec.y : (rb == 1 ? rec.z : (rb == 2 ? rec.w : 0));
                 const uint32_t next = (uint32_t)S.prev ^ nxa ^ nxb;
-                if (e == 0) { S.i0 = i3; S.p0 = p3; }
-                else if (e == 1) { S.i1 = i3; S.p1 = p3; }
-                else { S.i2 = i3; S.p2 = p3; }
+                if (e == 0) { S.i0 = i3; S.p0 = p3; S.m0 = m3; }
+                else if (e == 1) { S.i1 = i3; S.p1 = p3; S.m1 = m3; }
+                else { S.i2 = i3; S.p2 = p3; S.m2 = m3; }
                 if (BOUNDED) Z.set(e, x);
                 ++steps;
-                bool done = false;
-                uint32_t code = next;
-                const int32_t nt_ = MULTI ? sdesc[m].mesh.nt : mv0.nt;
+                code = next;
                 if (next & TM_CFACE_FLAG) {
                     done = true;
-                } else if (next >= (uint32_t)nt_) {
+                } else if (next >= (uint32_t)(MULTI ? sdesc[m].mesh.nt : mv0.nt)) {
                     done = true;
                     code = TM_BOUNDARY;
                     sc.flags |= TM_HIT_BAD_ID;
@@ -342,16 +387,16 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
                 } else if (BOUNDED && Z.beyond()) {
                     done = true;
                     code = TM_BOUNDARY;
-                }
-                if (done) {
-                    const MeshView &mv = MULTI ? sdesc[m].mesh : mv0;
-                    tm_hit *hp = MULTI ? sdesc[m].hits + local : hits0 + local;
-                    finish<MODE>(mv, rp, hp, code, S.tet, steps, sc.flags, mv.extent * (1.0f / 64.0f));
-                    active = false;
                 } else {
                     S.prev = S.tet;
                     S.tet = (int32_t)next;
                 }
+            }
+            if (done) {
+                finish_ray<MODE>(MULTI ? sdesc[m].mesh : mv0, sc.ray,
+                                 MULTI ? sdesc[m].hits + local : hits0 + local, code, S.tet, steps,
+                                 sc.flags);
+                active = false;
             }
         }
     }
@@ -428,9 +473,9 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.tau = (o && o->guard_tau > 0.f) ? o->guard_tau : 1e-6f;
     const double side = std::cbrt((double)(nt > 0 ? nt : 1));
     c.max_steps = (o && o->max_steps) ? o->max_steps : (uint32_t)(4.0 * side * 8.0 + 256.0);
-    c.block = (o && o->block) ? o->block : 256;
-    c.refill = (o && o->refill) ? o->refill : 16;
-    c.batch_steps = (o && o->batch_steps) ? o->batch_steps : 8;
+    c.block = (o && o->block) ? o->block : 512;
+    c.refill = (o && o->refill) ? o->refill : 8;
+    c.batch_steps = (o && o->batch_steps) ? o->batch_steps : 16;
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
     return c;
@@ -438,7 +483,7 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
 
 static bool valid_config(const TraceConfig &c) {
     return (c.mode == FP32G || c.mode == FP32 || c.mode == FP64) && c.block >= 32 &&
-           c.block <= 512 && c.block % 32 == 0 && c.refill >= 1 && c.refill <= 32 &&
+           c.block <= 1024 && c.block % 32 == 0 && c.refill >= 1 && c.refill <= 32 &&
            c.batch_steps >= 1 && c.batch_steps <= 256 && c.ctas_per_sm >= 0;
 }
 

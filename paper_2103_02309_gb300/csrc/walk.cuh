@@ -127,6 +127,11 @@ __device__ TM_GUARD_ATTR static double guard_det(const tm_ray *ray, const float4
     return det2(pa, pb);
 }
 
+// tau * max(|p.x|, |p.y|): the guard threshold contribution of one point.
+template <class R> __device__ __forceinline__ float guard_mag(const P2<R> &p, float tau) {
+    return tau * fmaxf(fabsf((float)p.x), fabsf((float)p.y));
+}
+
 // Everything the sign tests of one ray need besides the two points.
 struct SignCtx {
     const tm_ray *ray;
@@ -142,15 +147,16 @@ __device__ __forceinline__ bool pos(const P2<R> &a, const P2<R> &b, int32_t ia, 
                                     SignCtx &c) {
     const R d = det2(a, b);
     if (MODE == FP32G) {
-        const float m = fmaxf(fmaxf(fabsf((float)a.x), fabsf((float)a.y)),
-                              fmaxf(fabsf((float)b.x), fabsf((float)b.y)));
-        if (fabsf((float)d) < c.tau * m) {
+        // threshold tau * max|coordinate| of the pair, the same rule as step_signs()
+        const float t = fmaxf(guard_mag(a, c.tau), guard_mag(b, c.tau));
+        if (!(fabsf((float)d) > t)) {
             c.flags |= TM_HIT_GUARD;
             const double dd = guard_det(c.ray, c.pts, ia, ib);
             if (dd != 0.0) return dd > 0.0;
             c.flags |= TM_HIT_TIE;
             return ia < ib;
         }
+        return d > R(0);
     }
     if (d != R(0)) return d > R(0);
     c.flags |= TM_HIT_TIE;
@@ -172,7 +178,10 @@ template <class R> struct WalkState {
     int32_t tet, prev;
     int32_t i0, i1, i2;
     P2<R> p0, p1, p2;
+    float m0, m1, m2;  // guard mode: tau * max(|p.x|, |p.y|) of each slot
 };
+
+
 
 // Exit face of tet T for the ray's line (Sec. 4: "at most four point in
 // triangle tests in 2-D"): the face, other than `skip`, whose projection
@@ -218,16 +227,19 @@ __device__ __forceinline__ bool line_init(const MeshView &mv, const Basis<R> &B,
         }
     }
     S.prev = T;
+    S.m0 = guard_mag(S.p0, c.tau);
+    S.m1 = guard_mag(S.p1, c.tau);
+    S.m2 = guard_mag(S.p2, c.tau);
     return true;
 }
 
 // The rare restart fallback: one 3-D face-plane step in double precision
 // (exit through the face plane with the smallest positive crossing, the
 // entry face excluded), used only when the line misses the restart tet by
-// rounding.  Returns the raw neighbour value crossed and the local index
-// of the shared face inside the neighbour (or -1).
-__device__ __noinline__ static uint32_t step3d(const MeshView &mv, const tm_ray *ray, int32_t T,
-                                               int skip, int *skip_next) {
+// rounding.  Returns the raw neighbour value crossed (x) and the local index
+// of the shared face inside the neighbour (y, or -1).
+__device__ __noinline__ static int2 step3d(const MeshView &mv, const tm_ray *ray, int32_t T,
+                                           int skip) {
     const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
     const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
     const double o[3] = {w0.x, w0.y, w0.z}, d[3] = {w1.x, w1.y, w1.z};
@@ -254,16 +266,84 @@ __device__ __noinline__ static uint32_t step3d(const MeshView &mv, const tm_ray 
             if (best < 0 || tk < tb) { best = k; tb = tk; }
         }
     }
-    *skip_next = -1;
-    if (best < 0) return TM_BOUNDARY;
+    int skip_next = -1;
+    if (best < 0) return make_int2((int)TM_BOUNDARY, -1);
     const uint32_t nb = NB[best];
-    if (!(nb & TM_CFACE_FLAG)) {
+    if (!(nb & TM_CFACE_FLAG) && nb < (uint32_t)mv.nt) {
         const int4 un = __ldg(mv.cold + 2 * (int32_t)nb + 1);
         const int32_t UN[4] = {un.x, un.y, un.z, un.w};
         for (int k = 0; k < 4; ++k)
-            if (UN[k] == T) *skip_next = k;
+            if (UN[k] == T) skip_next = k;
     }
-    return nb;
+    return make_int2((int)nb, skip_next);
+}
+
+// Guard mode: the three sign tests of one step when at least one of them is
+// within its threshold (or exactly zero), re-decided from double-precision
+// projections of the two points (ties broken by vertex ids).  Out of line:
+// the rare path.  Returns the three signs in bits 0..2 and TM_HIT_GUARD /
+// TM_HIT_TIE in bits 8 and up.
+__device__ __noinline__ static uint32_t guard_signs(const tm_ray *ray, const float4 *pts, float d0,
+                                                    float d1, float d2, float t0, float t1, float t2,
+                                                    int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
+    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
+    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
+    const Basis<double> B = make_basis<double>(w1.x, w1.y, w1.z, w0.x, w0.y, w0.z);
+    const float4 x3 = __ldg(pts + i3);
+    const P2<double> q3 = B.project(x3.x, x3.y, x3.z);
+    const float d[3] = {d0, d1, d2}, t[3] = {t0, t1, t2};
+    const int32_t id[3] = {i0, i1, i2};
+    uint32_t bits = 0, flags = 0;
+    for (int k = 0; k < 3; ++k) {
+        bool pos;
+        if (fabsf(d[k]) > t[k]) {
+            pos = d[k] > 0.f;
+        } else {
+            flags |= TM_HIT_GUARD;
+            const float4 x = __ldg(pts + id[k]);
+            const double dd = det2(q3, B.project(x.x, x.y, x.z));
+            if (dd != 0.0) {
+                pos = dd > 0.0;
+            } else {
+                flags |= TM_HIT_TIE;
+                pos = i3 < id[k];
+            }
+        }
+        bits |= (uint32_t)pos << k;
+    }
+    return bits | (flags << 8);
+}
+
+// The three sign tests of one step, det(p3, p_k) > 0 for the entry-face
+// slots k = 0, 1, 2 (bit k), with the same decision rule as pos().
+template <int MODE, class R>
+__device__ __forceinline__ uint32_t step_signs(const WalkState<R> &S, const P2<R> &p3, int32_t i3,
+                                               float m3, SignCtx &c) {
+    const R d0 = det2(p3, S.p0), d1 = det2(p3, S.p1), d2 = det2(p3, S.p2);
+    uint32_t bits = (uint32_t)(d0 > R(0)) | ((uint32_t)(d1 > R(0)) << 1) | ((uint32_t)(d2 > R(0)) << 2);
+    if (MODE == FP32G) {
+        const float t0 = fmaxf(m3, S.m0), t1 = fmaxf(m3, S.m1), t2 = fmaxf(m3, S.m2);
+        const bool amb = !(fabsf((float)d0) > t0) | !(fabsf((float)d1) > t1) | !(fabsf((float)d2) > t2);
+        if (amb) {
+            const uint32_t r = guard_signs(c.ray, c.pts, (float)d0, (float)d1, (float)d2, t0, t1, t2,
+                                           S.i0, S.i1, S.i2, i3);
+            c.flags |= r >> 8;
+            bits = r & 7u;
+        }
+    } else {
+        if ((d0 == R(0)) | (d1 == R(0)) | (d2 == R(0))) {
+            c.flags |= TM_HIT_TIE;
+            if (d0 == R(0)) bits |= (uint32_t)(i3 < S.i0);
+            if (d1 == R(0)) bits |= (uint32_t)(i3 < S.i1) << 1;
+            if (d2 == R(0)) bits |= (uint32_t)(i3 < S.i2) << 2;
+        }
+    }
+    return bits;
+}
+
+// Alg. 1 on the three signs: slot (0, 1, 2) that the new vertex replaces.
+__device__ __forceinline__ int exit_slot_bits(uint32_t s) {
+    return (s & 1u) ? ((s & 2u) ? 0 : 2) : ((s & 4u) ? 1 : 0);
 }
 
 // Does the closed tet T hold the ray origin (double precision, with a
@@ -292,14 +372,16 @@ __device__ __noinline__ static bool holds_origin(const MeshView &mv, const tm_ra
 }
 
 // Final ray-triangle test on the hit triangle in its own vertex order
-// (Moller & Trumbore 1997): t and (b1, b2).  In guard mode it is redone in
-// double precision when the float result is close to the origin relative to
-// the scene (t < extent/64, where cancellation in (v0 - o) dominates) or the
-// ray grazes the plane.
+// (Moller & Trumbore 1997): t and (b1, b2).  `cond` estimates how many
+// units of rounding the computed t may be off by (relative): the condition
+// numbers of t's denominator d.(e2 x e1) and numerator s.(e1 x e2), measured
+// with 1-norms, so cond * eps bounds the relative error of t up to a small
+// constant.  It is large for grazing rays and for origins close to the
+// triangle's plane far from its vertices.
 template <class R>
 __device__ __forceinline__ void mt_hit(const float4 &o4, const float4 &d4, const float4 &a4,
                                        const float4 &b4, const float4 &c4, R &t, R &b1, R &b2,
-                                       R &cosang) {
+                                       R &cond) {
     const R e1x = R(b4.x) - R(a4.x), e1y = R(b4.y) - R(a4.y), e1z = R(b4.z) - R(a4.z);
     const R e2x = R(c4.x) - R(a4.x), e2y = R(c4.y) - R(a4.y), e2z = R(c4.z) - R(a4.z);
     const R dx = d4.x, dy = d4.y, dz = d4.z;
@@ -307,14 +389,13 @@ __device__ __forceinline__ void mt_hit(const float4 &o4, const float4 &d4, const
     const R det = e1x * px + e1y * py + e1z * pz;
     const R sx = R(o4.x) - R(a4.x), sy = R(o4.y) - R(a4.y), sz = R(o4.z) - R(a4.z);
     const R qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    const R num = e2x * qx + e2y * qy + e2z * qz;
     const R inv = R(1) / det;
     b1 = (sx * px + sy * py + sz * pz) * inv;
     b2 = (dx * qx + dy * qy + dz * qz) * inv;
-    t = (e2x * qx + e2y * qy + e2z * qz) * inv;
-    // |cos| of the angle between d and the triangle normal
-    const R nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-    const R nn = sqrt(nx * nx + ny * ny + nz * nz), dn = sqrt(dx * dx + dy * dy + dz * dz);
-    cosang = fabs(nx * dx + ny * dy + nz * dz) / (nn * dn);
+    t = num * inv;
+    const R n1 = (fabs(e1x) + fabs(e1y) + fabs(e1z)) * (fabs(e2x) + fabs(e2y) + fabs(e2z));
+    cond = n1 * ((fabs(dx) + fabs(dy) + fabs(dz)) / fabs(det) + (fabs(sx) + fabs(sy) + fabs(sz)) / fabs(num));
 }
 
 }  // namespace tmk

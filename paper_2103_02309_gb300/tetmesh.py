@@ -95,7 +95,8 @@ def unpack_hits(h) -> dict:
 
 
 def make_camera(eye, fov_deg, width, height) -> N.Camera:
-    """Pinhole camera of the synthetic workloads (looking along +z)."""
+    """Pinhole camera of the synthetic workloads (looking along +z); the float32
+    constants are computed in float64 and rounded once."""
     c = N.Camera()
     for i in range(3):
         c.eye[i] = float(eye[i])

@@ -27,8 +27,8 @@ not available):
   i fastest, then the half.
 * Pinhole camera looking along +z, image x along +x, image y (downwards)
   along -y, field of view across the shorter image side, pixel centres at
-  (px+0.5, py+0.5).  Directions are formed and normalised in float64 and
-  rounded once to float32.  Rays are stored in warp tiles of 8x4 pixels,
+  (px+0.5, py+0.5).  Directions are formed and normalised with a fixed chain
+  of correctly rounded float32 operations (see camera_rays).  Rays are stored in warp tiles of 8x4 pixels,
   tiles in row-major order, pixels row-major inside a tile (ragged edge
   tiles keep only in-image pixels).
 
@@ -165,28 +165,31 @@ class Camera:
     height: int
 
     def constants(self):
-        """Host-side float64 constants of the pixel -> direction recipe."""
+        """float32 constants of the pixel -> direction recipe (computed in float64, rounded once)."""
         short = min(self.width, self.height)
         tanh = math.tan(math.radians(self.fov_deg) * 0.5)
-        return dict(kx=2.0 / self.width, ky=2.0 / self.height,
-                    tx=tanh * (self.width / short), ty=tanh * (self.height / short))
+        f = np.float32
+        return dict(kx=f(2.0 / self.width), ky=f(2.0 / self.height),
+                    tx=f(tanh * (self.width / short)), ty=f(tanh * (self.height / short)))
 
 
 def camera_rays(cam: Camera):
-    """Origins and unit directions (float32 [W*H, 3]) in warp-tile order.
+    """Origins and directions (float32 [W*H, 3]) in warp-tile order.
 
-    sx = ((px + 0.5)*kx - 1)*tx ; sy = (1 - (py + 0.5)*ky)*ty ;
-    s2 = (sx*sx + sy*sy) + 1 ; L = sqrt(s2) ; d = (sx/L, sy/L, 1/L)
-    every operation in float64 in this order, then one rounding to float32.
+    Every operation below is one correctly rounded float32 operation, in this
+    order (no fused multiply-add):
+      sx = ((px + 0.5)*kx - 1)*tx ; sy = (1 - (py + 0.5)*ky)*ty ;
+      s2 = (sx*sx + sy*sy) + 1 ; L = sqrt(s2) ; d = (sx/L, sy/L, 1/L)
     """
     c = cam.constants()
+    f = np.float32
     px, py = tile_order(cam.width, cam.height)
-    sx = ((px.astype(np.float64) + 0.5) * c["kx"] - 1.0) * c["tx"]
-    sy = (1.0 - (py.astype(np.float64) + 0.5) * c["ky"]) * c["ty"]
-    s2 = (sx * sx + sy * sy) + 1.0
+    sx = ((px.astype(f) + f(0.5)) * c["kx"] - f(1.0)) * c["tx"]
+    sy = (f(1.0) - (py.astype(f) + f(0.5)) * c["ky"]) * c["ty"]
+    s2 = (sx * sx + sy * sy) + f(1.0)
     L = np.sqrt(s2)
-    d = np.stack([sx / L, sy / L, 1.0 / L], axis=1).astype(np.float32)
-    o = np.broadcast_to(np.asarray(cam.eye, dtype=np.float32), d.shape).copy()
+    d = np.stack([sx / L, sy / L, f(1.0) / L], axis=1).astype(f)
+    o = np.broadcast_to(np.asarray(cam.eye, dtype=f), d.shape).copy()
     return o, d
 
 
