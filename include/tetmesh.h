@@ -224,6 +224,26 @@ tm_status tm_gen_secondary(const tm_mesh *mesh, const tm_hit *hits, int64_t n,
                            const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                            tm_ray *rays_out, int64_t *count_dev, int32_t *src_out, void *stream);
 
+/* The same as tm_gen_secondary, for callers that cannot allocate device
+ * memory while they run (a renderer with a fixed memory budget, or code
+ * inside a stream capture that must not add allocation nodes).  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its scan
+ * scratch is a static device array of this library, sized for at most
+ * TM_NOALLOC_MAX_HITS hits (about 192 KiB, held on every device that loads
+ * the library until the process exits).  n > TM_NOALLOC_MAX_HITS returns
+ * TM_ERR_TOO_LARGE (tm_last_error() says why) and launches nothing.
+ * The first call on each device looks up the array's device address; make
+ * that first call outside any stream capture.  All calls share the array,
+ * so calls whose work overlaps on the GPU (several streams or host
+ * threads) race on it: serialise them.  Nothing in the array needs to start
+ * at zero; each call writes every entry it later reads. */
+#define TM_NOALLOC_MAX_HITS (1 << 24)
+tm_status tm_gen_secondary_noalloc(const tm_mesh *mesh, const tm_hit *hits, int64_t n,
+                                   const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                                   tm_ray *rays_out, int64_t *count_dev, int32_t *src_out,
+                                   void *stream);
+
 /* Batched, uneven multi-mesh tracing in one persistent launch (a work
  * queue over all rays of all meshes), replayed from a CUDA graph.
  * tm_batch_create: meshes (HOST array of n_meshes uploaded meshes).

@@ -78,6 +78,7 @@ _SIGS = {
     "tm_trace": ([P, P, i64, P, P, ctypes.POINTER(TraceOpts), P], ctypes.c_int),
     "tm_gen_primary": ([ctypes.POINTER(Camera), P, f32, P, P], ctypes.c_int),
     "tm_gen_secondary": ([P, P, i64, P, ctypes.c_int, f32, u64, P, P, P, P], ctypes.c_int),
+    "tm_gen_secondary_noalloc": ([P, P, i64, P, ctypes.c_int, f32, u64, P, P, P, P], ctypes.c_int),
     "tm_batch_create": ([P, ctypes.c_int, ctypes.POINTER(P)], ctypes.c_int),
     "tm_batch_set": ([P, P, P, P, ctypes.POINTER(TraceOpts), i32], ctypes.c_int),
     "tm_batch_run": ([P, P], ctypes.c_int),

@@ -170,4 +170,17 @@ tm_status tm_gen_secondary(const tm_mesh *m, const tm_hit *hits, int64_t n, cons
                                 src_out, (cudaStream_t)stream);
 }
 
+tm_status tm_gen_secondary_noalloc(const tm_mesh *m, const tm_hit *hits, int64_t n,
+                                   const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                                   tm_ray *rays_out, int64_t *count_dev, int32_t *src_out,
+                                   void *stream) {
+    if (!m || n < 0 || per_hit < 1 || per_hit > 1024 || !count_dev || (n > 0 && (!hits || !rays_out)))
+        return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if (!m->on_device) return TM_ERR_NO_DEVICE;
+    if (n * (int64_t)per_hit > INT32_MAX) return TM_ERR_TOO_LARGE;
+    return launch_gen_secondary_noalloc(mesh_view(m), hits, n, n_dev, per_hit, tmax, seed, rays_out,
+                                        count_dev, src_out, (cudaStream_t)stream);
+}
+
 }  // extern "C"

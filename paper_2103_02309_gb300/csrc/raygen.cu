@@ -3,6 +3,9 @@
 // faces into the arrival-side tet (Sec. 6 of the paper), compacted in hit
 // order with a three-pass scan (count per block, scan of the block counts,
 // emit), so the output order does not depend on scheduling.
+#include <mutex>
+#include <string>
+
 #include "tm_internal.h"
 
 namespace tmk {
@@ -210,3 +213,88 @@ tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n
     return TM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Secondary-ray generation without allocation.
+//
+// Some callers cannot allocate device memory while they run, e.g. a renderer
+// that owns a fixed memory budget or code running inside a stream capture
+// that must not create allocation nodes.  tm_gen_secondary_noalloc does the
+// same work as tm_gen_secondary, but its scan scratch (per-block hit counts
+// and offsets) lives in the static device array below instead of
+// cudaMallocAsync memory.  The array holds the scratch for at most
+// TM_NOALLOC_MAX_HITS hits, about 192 KiB, and stays on every device that
+// loads this library until the process exits.
+//
+// The array is shared by every call: calls whose work overlaps on the GPU
+// (other streams, other host threads) race on it.  Nothing in it needs to
+// start at zero; each call writes every entry it later reads.
+namespace {
+
+constexpr int64_t kNoallocBlocks = (TM_NOALLOC_MAX_HITS + tmk::kScanBlock - 1) / tmk::kScanBlock;
+constexpr size_t kNoallocCountBytes = ((sizeof(int32_t) * kNoallocBlocks + 255) / 256) * 256;
+constexpr size_t kNoallocBytes = kNoallocCountBytes + sizeof(int64_t) * (kNoallocBlocks + 1);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in and is never passed to
+// a kernel).
+tm_status noalloc_scratch(void **addr) {
+    int dev = 0;
+    TM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        tm_set_error_text("tm_gen_secondary_noalloc: device ordinal out of range");
+        return TM_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            tm_set_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+            return TM_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *addr = g_noalloc_addr[dev];
+    return TM_OK;
+}
+
+}  // namespace
+
+tm_status launch_gen_secondary_noalloc(const MeshView &mv, const tm_hit *hits, int64_t n,
+                                       const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                                       tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
+    using tmk::kScanBlock;
+    if (n > TM_NOALLOC_MAX_HITS) {
+        tm_set_error_text("tm_gen_secondary_noalloc: " + std::to_string(n) +
+                          " hits exceed the static scratch capacity of " +
+                          std::to_string((long long)TM_NOALLOC_MAX_HITS));
+        return TM_ERR_TOO_LARGE;
+    }
+    void *base = nullptr;
+    const tm_status st = noalloc_scratch(&base);
+    if (st != TM_OK) return st;
+    if (n == 0) {
+        TM_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
+        return TM_OK;
+    }
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    int32_t *counts = static_cast<int32_t *>(base);
+    int64_t *offsets = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(base) + kNoallocCountBytes);
+    tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, counts);
+    tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb, offsets, per_hit, count);
+    tmk::emit_secondary_kernel<<<(int)nb, kScanBlock, 0, s>>>(mv, hits, n, n_dev, offsets, per_hit,
+                                                             tmax, seed, out, src);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tm_set_error("gen_secondary (no allocation) launch", e);
+        return TM_ERR_CUDA;
+    }
+    tm_count_launches(3);
+    return TM_OK;
+}

@@ -98,6 +98,10 @@ tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n
                                const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                                tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s);
 
+tm_status launch_gen_secondary_noalloc(const MeshView &mv, const tm_hit *hits, int64_t n,
+                                       const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                                       tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s);
+
 // Multi-mesh persistent trace over a device descriptor table.
 struct BatchDesc {
     MeshView mesh;
