@@ -38,12 +38,12 @@ UNIT = "Mrays/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 RAY_BYTES, HIT_BYTES = 32, 32
-# algorithmic bytes: per tet step one Tet16 record + one float4 point; per ray the
-# ray record, the hit record, the start tet's cold record and its four points;
-# per hit the constrained-face record and the triangle's three points.
+# Algorithmic bytes of the walk kernel (the dominant kernel): per tet step one
+# Tet16 record and one float4 point; per ray its start record (32 B, in the
+# hit slot), the ray (32 B), the three entry-face points (48 B) and the end
+# record (32 B).
 STEP_BYTES = 16 + 16
-RAY_FIXED_BYTES = RAY_BYTES + HIT_BYTES + 32 + 4 * 16
-HIT_EXTRA_BYTES = 32 + 3 * 16
+WALK_RAY_BYTES = 32 + RAY_BYTES + 3 * 16 + 32
 
 WORKLOADS = {
     "tiny": dict(desc="8^3-cell Kuhn grid (3,072 tets), one sphere, 64x64 primary rays + 1 cosine "
@@ -57,6 +57,9 @@ WORKLOADS = {
     "large": dict(desc="256^3-cell Kuhn grid (100,663,296 tets), 256 random spheres, 1024x1024 "
                        "primary rays + 8 ambient-occlusion rays per hit (t_max 0.05)",
                   per_hit=8, tmax=0.05, kind="ao"),
+    "batched": dict(desc="32 meshes of 16^3..96^3 cells with 4-32 random spheres each, 1K-2M rays "
+                         "per mesh (log-uniform), half camera rays and half uniform-direction rays "
+                         "from located interior points", per_hit=0, tmax=float("inf"), kind="none"),
 }
 
 
@@ -96,7 +99,7 @@ def measured_hbm():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("trace.cu", "walk.cuh"):
+    for f in ("trace.cu", "walk.cuh"):  # the walk kernel's sources
         with open(os.path.join(ROOT, "paper_2103_02309_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -104,7 +107,7 @@ def kernel_source_sha():
 
 def profiled_traffic(workload):
     """DRAM bytes per trace launch from the committed ncu summary, if it matches the source."""
-    path = os.path.join(ROOT, "profiles", f"trace_kernel_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"walk_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -214,45 +217,44 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def opts(mode):
-        return tmx.trace_opts(mode=mode, block=args.block, refill=args.refill,
-                              batch_steps=args.batch_steps, tmax_early_exit=math.isfinite(W["tmax"]))
+    ev_p = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev_p + ev_b:
+        e.record(stream)                                  # materialise the CUDA events
+    torch.cuda.synchronize()
 
-    def step(o, ev=None):
+    def opts(mode, ev=None):
+        return tmx.trace_opts(mode=mode, block=args.block, refill=args.refill,
+                              batch_steps=args.batch_steps, tmax_early_exit=math.isfinite(W["tmax"]),
+                              phase_events=ev)
+
+    def step(op, ob):
         mesh.locate(eye, out=start)
         tmx.gen_primary(cam, start, rays=rays)
-        if ev:
-            ev[0].record(stream)
-        mesh.trace(rays, hits=hits, opts=o)
-        if ev:
-            ev[1].record(stream)
+        mesh.trace(rays, hits=hits, opts=op)
         mesh.gen_secondary(hits, per_hit, W["tmax"], seed=0x5EED, rays_out=rays2, count=count)
-        if ev:
-            ev[2].record(stream)
-        mesh.trace(rays2, hits=hits2, n_dev=count, opts=o)
-        if ev:
-            ev[3].record(stream)
+        mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
 
     def timed(mode, steps, warmup):
-        o = opts(mode)
+        op, ob = opts(mode, ev_p), opts(mode, ev_b)
         for _ in range(warmup):
-            step(o)
+            step(op, ob)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         l0 = tmx.launch_count()
-        tot, trace_ms = 0.0, 0.0
+        tot, trace_ms, walk_ms = 0.0, 0.0, 0.0
         for _ in range(steps):
             flush.zero_()                                  # evict the mesh from L2 between steps
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             e0.record(stream)
-            step(o, ev)
+            step(op, ob)
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-            trace_ms += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+            trace_ms += ev_p[0].elapsed_time(ev_p[3]) + ev_b[0].elapsed_time(ev_b[3])
+            walk_ms += ev_p[1].elapsed_time(ev_p[2]) + ev_b[1].elapsed_time(ev_b[2])
         torch.cuda.synchronize()
         launches = tmx.launch_count() - l0
         if world > 1:
@@ -260,41 +262,45 @@ def run_ours(args, world, rank, local):
             t = torch.tensor([tot], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             tot = float(t.item())
-        return tot / steps, trace_ms / steps, launches
+        return tot / steps, trace_ms / steps, walk_ms / steps, launches
 
     # headline arm: FP32 walk with FP64 guard
     with ClockSampler(local) as clk:
-        ms, trace_ms, launches = timed("fp32g", args.steps, max(args.warmup, 3))
+        ms, trace_ms, walk_ms, launches = timed("fp32g", args.steps, max(args.warmup, 3))
     n_second = int(count.item())
     rays_per_step = n_primary + n_second
     g1 = tmx.unpack_hits(hits)
     g2 = tmx.unpack_hits(hits2[:n_second])
     steps_total = int(g1["steps"].astype(np.int64).sum() + g2["steps"].astype(np.int64).sum())
-    n_hits = int((g1["tri"] >= 0).sum() + (g2["tri"] >= 0).sum())
-    alg_bytes = steps_total * STEP_BYTES + rays_per_step * RAY_FIXED_BYTES + n_hits * HIT_EXTRA_BYTES
+    alg_bytes = steps_total * STEP_BYTES + rays_per_step * WALK_RAY_BYTES
     guard_rate = float(((g1["flags"] & tmx.HIT_GUARD) != 0).mean())
+    fl = np.concatenate([g1["flags"], g2["flags"]])
+    slow_rate = float(((fl & tmx.HIT_SLOW_PASS) != 0).mean())
     final64_rate = float(((np.concatenate([g1["flags"], g2["flags"]]) & tmx.HIT_FINAL_FP64) != 0).mean())
     value = world * rays_per_step / (ms * 1e-3) / 1e6
 
     hbm, hbm_src = measured_hbm()
-    achieved = alg_bytes / (trace_ms * 1e-3) / 1e9
+    achieved = alg_bytes / (walk_ms * 1e-3) / 1e9
     traffic = profiled_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "trace_kernel (primary + bounce launches)",
-                "algorithmic_bytes_per_step": alg_bytes,
+                "kernel": "walk_kernel (primary + bounce launches; bytes and time per step)",
+                "algorithmic_bytes_per_launch": alg_bytes // 2,
+                "walk_ms_per_launch": round(walk_ms / 2, 4),
                 "tet_steps_per_step": steps_total,
+                "walk_share_of_step": round(walk_ms / ms, 4),
                 "trace_share_of_step": round(trace_ms / ms, 4)}
 
     arms = {}
     if not args.no_arms:
         keep = (hits.clone(), hits2.clone(), n_second)
         for mode in ("fp64", "fp32"):
-            ams, atr, _ = timed(mode, max(2, args.steps // 3), 1)
+            ams, atr, awk, _ = timed(mode, max(2, args.steps // 3), 1)
             arms[mode] = {"value": round(world * (n_primary + int(count.item())) / (ams * 1e-3) / 1e6, 2),
-                          "ms_per_step": round(ams, 3), "trace_ms": round(atr, 3)}
+                          "ms_per_step": round(ams, 3), "trace_ms": round(atr, 3),
+                          "walk_ms": round(awk, 3)}
             if mode == "fp64":
                 a1 = tmx.unpack_hits(hits)["tri"]
                 arms[mode]["primary_id_agreement_vs_fp32g"] = float((a1 == g1["tri"]).mean())
@@ -321,7 +327,8 @@ def run_ours(args, world, rank, local):
                        "order": args.order, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between steps (256 MiB write outside the step events)",
                        "build_s": round(build_s, 2),
-                       "guard_rate_primary": guard_rate, "final_fp64_rate": final64_rate},
+                       "guard_rate_primary": guard_rate, "slow_pass_rate": slow_rate,
+                       "final_fp64_rate": final64_rate},
             "roofline": roofline, "arms": arms, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
         }
@@ -457,11 +464,92 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, world, rank, local):
+    """32 uneven meshes: one persistent graph-replayed launch vs 32 separate launches."""
+    import torch
+    from paper_2103_02309_gb300 import build as libbuild
+    libbuild.build()
+    torch.cuda.set_device(local)
+    import scenegen as sg
+    from paper_2103_02309_gb300 import tetmesh as tmx
+    dev = torch.device("cuda", local)
+    descs = sg.batched_meshes()
+    meshes, rays, hits = [], [], []
+    t0 = time.time()
+    for dsc in descs:
+        s = sg.make_grid_scene("batched", dsc["n"], sg.BATCHED["jitter"], dsc["seed"],
+                               n_spheres=dsc["n_spheres"])
+        mesh = tmx.Mesh(s.points, s.tets, s.tris)
+        n_prim = dsc["primary"]
+        side = max(1, int(math.ceil(math.sqrt(n_prim))))
+        cam = tmx.make_camera(sg.BATCHED["camera_eye"], sg.BATCHED["fov_deg"], side,
+                              max(1, int(math.ceil(n_prim / side))))
+        eye = torch.tensor([sg.BATCHED["camera_eye"]], dtype=torch.float32, device=dev)
+        r1 = tmx.gen_primary(cam, mesh.locate(eye))
+        n_uni = dsc["rays"] - n_prim
+        q = torch.from_numpy(sg.interior_points(n_uni, dsc["seed"])).to(dev)
+        tet = mesh.locate(q)
+        d = sg.uniform_directions(n_uni, dsc["seed"])
+        r2 = torch.empty((n_uni, 8), dtype=torch.float32, device=dev)
+        r2[:, 0:3] = q
+        r2[:, 4:7] = torch.from_numpy(d).to(dev)
+        r2[:, 7] = float("inf")
+        r2.view(torch.int32)[:, 3] = tet
+        r = torch.cat([r1, r2]).contiguous()
+        meshes.append(mesh)
+        rays.append(r)
+        hits.append(torch.empty((r.shape[0], 8), dtype=torch.int32, device=dev))
+    build_s = time.time() - t0
+    total = sum(int(r.shape[0]) for r in rays)
+    b = tmx.Batch(meshes)
+    b.set(rays, hits)
+    tuned = b.autotune(reps=2)
+    stream = torch.cuda.current_stream()
+
+    def timeit(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        l0 = tmx.launch_count()
+        tot = 0.0
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / steps, tmx.launch_count() - l0
+
+    with ClockSampler(local) as clk:
+        ms_graph, launches = timeit(b.run, args.steps)
+    ms_sep, _ = timeit(b.run_separate, args.steps)
+    value = total / (ms_graph * 1e-3) / 1e6
+    line = {"metric": "Mrays/s, 32-mesh uneven batch in one persistent graph launch", "value": round(value, 2),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 3,
+            "ms_per_step": round(ms_graph, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched: {WORKLOADS['batched']['desc']}", "rays": total,
+                       "meshes": len(meshes), "tets": int(sum(m.n_tets for m in meshes)),
+                       "build_s": round(build_s, 1),
+                       "autotuned": {"block": tuned.opts.block, "refill": tuned.opts.refill,
+                                     "batch_steps": tuned.opts.batch_steps,
+                                     "sort_chunk": tuned.sort_chunk, "ms": round(tuned.ms, 3)}},
+            "separate_launches": {"value": round(total / (ms_sep * 1e-3) / 1e6, 2),
+                                  "ms_per_step": round(ms_sep, 3)},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            run_batched(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

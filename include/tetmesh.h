@@ -103,6 +103,8 @@ typedef struct {
 #define TM_HIT_BAD_ID     0x80u  /* an id read from the mesh was out of range (corrupt mesh); miss */
 #define TM_HIT_START_MOVED 0x100u /* the origin lay on the start tet's boundary; the walk started
                                      in a neighbouring tet that also holds it */
+#define TM_HIT_SLOW_PASS  0x200u  /* guard mode: at least one step had a sign test within the
+                                     guard threshold and was re-decided out of line */
 
 typedef struct {
     int32_t order;           /* TM_ORDER_HILBERT (default) or TM_ORDER_INPUT */
@@ -119,6 +121,9 @@ typedef struct {
     int32_t ctas_per_sm; /* persistent CTAs per SM: 0 (as many as fit) */
     int32_t tmax_early_exit; /* nonzero: stop a walk once its entry face lies beyond t_max
                                 (worth it for short rays, e.g. ambient occlusion) */
+    void *phase_events[4];   /* optional cudaEvent_t handles recorded on the stream before the
+                                start phase, after it, after the walk and after the finish
+                                phase (tm_trace only); NULL entries are skipped */
 } tm_trace_opts;
 
 /* Mesh description returned by tm_mesh_info.  Device pointers are owned by
@@ -180,12 +185,17 @@ tm_status tm_map_ids(const tm_mesh *mesh, int kind, int direction, const int32_t
  * exit plane lies beyond q[i]; writes its internal id to tet_out[i] (DEVICE
  * int32 [n]), or -1 when q[i] is outside the mesh or the walk exceeds its
  * bound.  hint (DEVICE int32 [n], may be NULL) gives a per-point source tet;
- * otherwise `source` (an internal id, or -1 for the mesh's default). */
+ * otherwise `source` (an internal id), or with source = -1 the located tet of
+ * the nearest point of a 16^3 lattice over the bounding box (located once
+ * when the mesh is uploaded), so that walks stay short. */
 tm_status tm_locate(const tm_mesh *mesh, const float *q, int64_t n, const int32_t *hint,
                     int32_t source, int32_t *tet_out, void *stream);
 
-/* Traces n DEVICE rays into n DEVICE hits (Sec. 4 + Sec. 7): one persistent
- * launch; warps refill idle lanes from a global ray cursor.  If n_dev is not
+/* Traces n DEVICE rays into n DEVICE hits (Sec. 4 + Sec. 7) in three
+ * launches: per-ray start (basis, start-tet exit face or face restart), a
+ * persistent walk whose warps refill idle lanes from a global ray cursor,
+ * and per-ray finish (the hit); the hit buffer carries the per-ray state
+ * between them.  If n_dev is not
  * NULL it points to a DEVICE int64 holding the ray count (read by the
  * kernel, clamped to n), so that counts produced on the device need no host
  * round trip.  opts may be NULL (defaults).  rays and hits must be 16-byte

@@ -47,7 +47,7 @@ class BuildOpts(ctypes.Structure):
 class TraceOpts(ctypes.Structure):
     _fields_ = [("mode", i32), ("guard_tau", f32), ("max_steps", ctypes.c_uint32), ("block", i32),
                 ("refill", i32), ("batch_steps", i32), ("ctas_per_sm", i32),
-                ("tmax_early_exit", i32)]
+                ("tmax_early_exit", i32), ("phase_events", P * 4)]
 
 
 class MeshInfo(ctypes.Structure):

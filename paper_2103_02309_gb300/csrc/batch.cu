@@ -19,7 +19,8 @@ struct tm_batch {
     std::vector<int64_t> perm_cap;
     int4 *d_chunks = nullptr;  // (mesh, first ray, count, 0) per sort chunk
     int64_t n_chunks = 0, chunks_cap = 0;
-    unsigned long long *d_cursor = nullptr;
+    unsigned long long *d_cursor = nullptr;  // walk scratch (counters + parked list)
+    size_t cursor_bytes = 0;
     TraceConfig cfg{};
     int32_t sort_chunk = 0;
     int64_t total = 0;
@@ -102,7 +103,7 @@ tm_status build_graph(tm_batch *b) {
     }
     st = launch_trace_batch(b->d_descs, (int)b->meshes.size(), b->total, b->cfg, b->d_cursor,
                             b->cap_stream, false);
-    if (b->total > 0) ++kernels;
+    if (b->total > 0) kernels += 3;  // start, walk, finish
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     if (st != TM_OK) {
@@ -141,11 +142,12 @@ tm_status tm_batch_create(const tm_mesh *const *meshes, int n_meshes, tm_batch *
     b->perm_cap.assign((size_t)n_meshes, 0);
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_descs, sizeof(BatchDesc) * (size_t)n_meshes)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_cursor, sizeof(unsigned long long))) != cudaSuccess) {
+        (e = cudaMalloc(&b->d_cursor, batch_scratch_bytes(0))) != cudaSuccess) {
         tm_set_error("cudaMalloc", e);
         tm_batch_destroy(b);
         return TM_ERR_CUDA;
     }
+    b->cursor_bytes = batch_scratch_bytes(0);
     b->cfg = resolve_trace_opts(nullptr, 1);
     *out = b;
     return TM_OK;
@@ -184,6 +186,12 @@ tm_status tm_batch_set(tm_batch *b, const tm_ray *const *rays, const int64_t *n,
         offset += n[i];
     }
     b->total = offset;
+    if (batch_scratch_bytes(offset) > b->cursor_bytes) {
+        cudaFree(b->d_cursor);
+        b->d_cursor = nullptr;
+        TM_CUDA(cudaMalloc(&b->d_cursor, batch_scratch_bytes(offset)));
+        b->cursor_bytes = batch_scratch_bytes(offset);
+    }
     b->cfg = resolve_trace_opts(opts, max_nt);
     b->sort_chunk = sort_chunk;
     b->n_chunks = (int64_t)chunks.size();

@@ -390,6 +390,34 @@ tm_status tm_upload(tm_mesh *m) {
                            cudaMemcpyHostToDevice));
     m->device_bytes = (int64_t)(b_tet + b_pts + b_cold + b_cf);
     m->on_device = true;
+    // seed lattice: locate the centres of a kSeedGrid^3 lattice over the
+    // bounding cube once, from the default source tet
+    const int G = kSeedGrid, ns = G * G * G;
+    std::vector<float> q((size_t)ns * 3);
+    for (int k = 0; k < G; ++k)
+        for (int j = 0; j < G; ++j)
+            for (int i = 0; i < G; ++i) {
+                const size_t c = (size_t)(i + G * (j + G * k));
+                q[3 * c + 0] = (float)(m->lo[0] + (i + 0.5) * m->extent / G);
+                q[3 * c + 1] = (float)(m->lo[1] + (j + 0.5) * m->extent / G);
+                q[3 * c + 2] = (float)(m->lo[2] + (k + 0.5) * m->extent / G);
+            }
+    float *d_q = nullptr;
+    TM_CUDA(cudaMalloc(&m->d_seeds, sizeof(int32_t) * ns));
+    TM_CUDA(cudaMalloc(&d_q, sizeof(float) * 3 * ns));
+    TM_CUDA(cudaMemcpy(d_q, q.data(), sizeof(float) * 3 * ns, cudaMemcpyHostToDevice));
+    MeshView mv = mesh_view(m);
+    mv.seeds = nullptr;  // the lattice itself is located from the default source
+    const uint32_t bound = (uint32_t)(64.0 * std::cbrt((double)m->nt) * 8.0 + 1024.0);
+    tm_status st = launch_locate(mv, d_q, ns, nullptr, m->source_tet, m->d_seeds, bound, 0);
+    cudaError_t e2 = cudaDeviceSynchronize();
+    cudaFree(d_q);
+    if (st != TM_OK) return st;
+    if (e2 != cudaSuccess) {
+        tm_set_error("seed lattice", e2);
+        return TM_ERR_CUDA;
+    }
+    m->device_bytes += (int64_t)(sizeof(int32_t) * ns);
     return TM_OK;
 }
 
@@ -403,6 +431,8 @@ void tm_free_device(tm_mesh *m) {
     cudaFree(m->d_pts);
     cudaFree(m->d_cold);
     cudaFree(m->d_cface);
+    cudaFree(m->d_seeds);
+    m->d_seeds = nullptr;
     m->d_tet16 = nullptr;
     m->d_pts = nullptr;
     m->d_cold = nullptr;

@@ -137,9 +137,11 @@ tm_status tm_locate(const tm_mesh *m, const float *q, int64_t n, const int32_t *
                     int32_t *tet_out, void *stream) {
     if (!m || n < 0 || (n > 0 && (!q || !tet_out))) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
-    if (source < 0 || source >= m->nt) source = m->source_tet;
+    MeshView mv = mesh_view(m);
+    if (source >= 0 && source < m->nt) mv.seeds = nullptr;  // an explicit source overrides the lattice
+    else source = m->source_tet;
     const uint32_t bound = (uint32_t)(64.0 * std::cbrt((double)m->nt) * 8.0 + 1024.0);
-    return launch_locate(mesh_view(m), q, n, hint, source, tet_out, bound, (cudaStream_t)stream);
+    return launch_locate(mv, q, n, hint, source, tet_out, bound, (cudaStream_t)stream);
 }
 
 tm_status tm_trace(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_t *n_dev,

@@ -112,7 +112,15 @@ locate_kernel(const __grid_constant__ MeshView mv, const float *__restrict__ q, 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float qx = q[3 * i], qy = q[3 * i + 1], qz = q[3 * i + 2];
-        int32_t T = hint ? hint[i] : source;
+        int32_t T = hint ? hint[i] : -1;
+        if ((T < 0 || T >= mv.nt) && mv.seeds) {
+            // the located tet of the lattice cell that holds q
+            const int G = kSeedGrid;
+            const int ci = min(max((int)((qx - mv.lo[0]) * mv.cell_inv), 0), G - 1);
+            const int cj = min(max((int)((qy - mv.lo[1]) * mv.cell_inv), 0), G - 1);
+            const int ck = min(max((int)((qz - mv.lo[2]) * mv.cell_inv), 0), G - 1);
+            T = __ldg(mv.seeds + ci + G * (cj + G * ck));
+        }
         if (T < 0 || T >= mv.nt) T = source;
         int32_t r = locate_walk<FP32>(mv, T, qx, qy, qz, max_steps);
         if (r < 0) r = locate_walk<FP64>(mv, T, qx, qy, qz, max_steps);

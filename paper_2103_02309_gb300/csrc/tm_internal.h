@@ -35,8 +35,13 @@ struct tm_mesh {
     float4 *d_pts = nullptr;
     int4 *d_cold = nullptr;
     int4 *d_cface = nullptr;
+    int32_t *d_seeds = nullptr;  // located tets of a kSeedGrid^3 lattice over the bounding box
     int64_t device_bytes = 0;
 };
+
+// Point location starts from the located tet of the nearest lattice point
+// (a coarse grid of precomputed source tets) instead of one fixed source.
+constexpr int kSeedGrid = 16;
 
 // What a kernel needs to walk one mesh.
 struct MeshView {
@@ -46,6 +51,8 @@ struct MeshView {
     const int4 *cface;
     int32_t nt, np, nc;
     float extent;
+    const int32_t *seeds;  // kSeedGrid^3 source tets for point location (may be null)
+    float lo[3], cell_inv;  // lattice origin and kSeedGrid / extent
 };
 
 inline MeshView mesh_view(const tm_mesh *m) {
@@ -58,6 +65,9 @@ inline MeshView mesh_view(const tm_mesh *m) {
     v.np = (int32_t)m->np;
     v.nc = (int32_t)m->nc;
     v.extent = (float)m->extent;
+    v.seeds = m->d_seeds;
+    for (int a = 0; a < 3; ++a) v.lo[a] = m->lo[a];
+    v.cell_inv = m->extent > 0 ? (float)(kSeedGrid / m->extent) : 0.f;
     return v;
 }
 
@@ -85,6 +95,7 @@ struct TraceConfig {
     int batch_steps;
     int ctas_per_sm;
     bool bounded;
+    cudaEvent_t events[4];
 };
 TraceConfig resolve_trace_opts(const tm_trace_opts *opts, int64_t nt);
 
@@ -111,7 +122,10 @@ struct BatchDesc {
     int64_t n;
     int64_t offset;       // first global ray index of this mesh
 };
-// `count`: add the launch to tm_launch_count (false while capturing a graph).
+// `count`: add the launches to tm_launch_count (false while capturing a graph).
+// `cursor` points to scratch of batch_scratch_bytes(total): the walk's ray
+// counter (zeroed by the launcher).
+inline size_t batch_scratch_bytes(int64_t) { return sizeof(unsigned long long); }
 tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t total,
                              const TraceConfig &cfg, unsigned long long *cursor, cudaStream_t s,
                              bool count);

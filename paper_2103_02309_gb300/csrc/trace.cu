@@ -1,23 +1,35 @@
-// Persistent ray traversal kernel (Sec. 4 and Sec. 7 of the paper) for sm_103a.
+// Ray traversal (Sec. 4 and Sec. 7 of the paper) for sm_103a, in three phases.
 //
-// One lane holds one ray in registers: its current tet, the tet it came
-// from, the entry face (three vertex ids and their 2-D projections) and the
-// scaled basis.  Each step (Alg. 6) reads one 16-byte Tet16 record and one
-// 16-byte point, projects the new vertex (Eq. 3 with the projected origin),
-// picks the exit slot with Alg. 1 and decodes the next tet from the xor
-// neighbours (Alg. 7):
-//   idx3 = idx0 ^ idx1 ^ idx2 ^ VX
-//   ra = rank of idx3, rb = rank of idx_exit among the four vertex ids
-//   N3 = ra == 3 ? prev : prev ^ NX_ra ;  next = rb == 3 ? N3 : N3 ^ NX_rb
-// and stops at a flagged (constrained or boundary) neighbour.  Alg. 1 is
-// evaluated from the three signs det(p3, p_k) without branches.
+//  1. start_kernel, one thread per ray: scaled basis and projected origin
+//     (Eq. 1-3, Sec. 7 optimisation 1), then the exit face of the start tet
+//     with at most four 2-D triangle tests (Sec. 4), or the restart through a
+//     hit face into the tet on its arrival side (Sec. 6).  It leaves a walk
+//     record in the ray's own hit slot.
+//  2. walk_kernel, persistent: the per-tet step (Alg. 6 / Alg. 7 with Alg. 1)
+//     until a flagged (constrained or boundary) neighbour; it leaves an end
+//     record in the hit slot.  Each step reads one 16-byte Tet16 record and
+//     one 16-byte point:
+//       idx3 = idx0 ^ idx1 ^ idx2 ^ VX
+//       ra = rank of idx3, rb = rank of idx_exit among the four vertex ids
+//       N3 = ra == 3 ? prev : prev ^ NX_ra ;  next = rb == 3 ? N3 : N3 ^ NX_rb
+//     Lanes whose ray ended are refilled from a global cursor once `refill`
+//     lanes are idle (ballot + popc, one atomicAdd per warp, ids handed out
+//     by rank within the idle mask), so the rays of one grab are consecutive
+//     and warps stay full (the persistent-threads scheme of Aila & Laine,
+//     "Understanding the efficiency of ray traversal on GPUs", HPG 2009).
+//     In guard mode the walk decides every sign test in float32; at a step
+//     where a test falls within the guard threshold the lane writes the ray's
+//     state back to its hit slot ("parks" it), and at its next refill it
+//     re-decides that one step out of line with the double-precision
+//     re-test, then continues from the new record.  No walk state is live
+//     across that call, so the step loop keeps a small register budget.
+//  3. finish_kernel, one thread per ray: the ray-triangle test on the hit
+//     triangle in its own vertex order, with the FP64 guard, into the hit.
 //
-// Warps are persistent: lanes whose ray ended are refilled from a global
-// cursor once `refill` lanes are idle (ballot + popc, one atomicAdd per
-// warp, the new ray ids handed out by rank within the idle mask), so that
-// the rays of one grab are consecutive and warps stay full as rays end after
-// different numbers of steps (the persistent-threads scheme of Aila & Laine,
-// "Understanding the efficiency of ray traversal on GPUs", HPG 2009).
+// Keeping the once-per-ray work out of the walk kernel keeps the walk's
+// register state small (no spills) and its code free of calls except the
+// rare FP64 re-test.  The hit slot (32 bytes per ray) carries the state
+// between the phases, so no scratch memory is needed beyond the cursor.
 #include <cmath>
 
 #include "walk.cuh"
@@ -27,86 +39,44 @@ namespace tmk {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBatch = 64;
 
-struct TraceParams {
+// The hit slot between the phases, 8 words:
+//   [0] phase (0: walk from here, 1: ended, 2: parked at tet [1] for a re-decided step)
+//   [1] tet (walk: tet to enter; ended: last tet)
+//   [2] prev (walk) or the flagged value that ended the walk (ended)
+//   [3..5] entry face ids, counter-clockwise in the ray's basis  [6] steps  [7] flags
+__device__ __forceinline__ void put_record(tm_hit *hp, int phase, int32_t tet, uint32_t prev_or_code,
+                                           int32_t i0, int32_t i1, int32_t i2, uint32_t steps,
+                                           uint32_t flags) {
+    reinterpret_cast<int4 *>(hp)[0] = make_int4(phase, tet, (int)prev_or_code, i0);
+    reinterpret_cast<int4 *>(hp)[1] = make_int4(i1, i2, (int)steps, (int)flags);
+}
+
+__device__ __forceinline__ void put_end(tm_hit *hp, int32_t tet, uint32_t code, uint32_t steps,
+                                        uint32_t flags) {
+    put_record(hp, 1, tet, code, -1, -1, -1, steps, flags);
+}
+
+// Which mesh and which ray a global ray index names (batched launches).
+struct Slot {
+    int32_t m, local;
+};
+__device__ __forceinline__ Slot find_slot(const BatchDesc *d, int n_meshes, unsigned long long r) {
+    int lo = 0, hi = n_meshes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)d[mid].offset <= r) lo = mid; else hi = mid - 1;
+    }
+    return Slot{lo, (int32_t)(r - (unsigned long long)d[lo].offset)};
+}
+
+struct PhaseParams {
     int64_t n_cap;
     const int64_t *n_dev;
-    unsigned long long *cursor;
-    uint32_t max_steps;
     float tau_rel;  // sign-test guard threshold relative to the mesh extent
-    int refill;
-    int batch_steps;
 };
 
-// Final hit in double precision: (t, b1, b2).  Out of line: the guard path.
-__device__ __noinline__ static float4 mt_hit_fp64(const float4 o4, const float4 d4, const float4 a4,
-                                                  const float4 b4, const float4 c4) {
-    double t, u, v, cond;
-    mt_hit<double>(o4, d4, a4, b4, c4, t, u, v, cond);
-    return make_float4((float)t, (float)u, (float)v, 0.f);
-}
-
-// In guard mode the float32 ray-triangle test is redone in double precision
-// when its condition estimate (see mt_hit) exceeds kFinalCond, i.e. when the
-// float32 t could be off by more than about 2e-6 relative.
-constexpr float kFinalCond = 32.f;
-
-// Writes the hit (or miss) of a finished ray.  `code` is the flagged
-// neighbour value that ended the walk in tet `tet`.
-template <int MODE>
-__device__ __forceinline__ void finish(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
-                                       uint32_t code, int32_t tet, uint32_t steps, uint32_t flags) {
-    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
-    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
-    int32_t tri = -1, cf = -1;
-    float t = __int_as_float(0x7f800000), b1 = 0.f, b2 = 0.f;
-    if (code != TM_BOUNDARY && (int32_t)(code & ~TM_CFACE_FLAG) >= mv.nc) {
-        flags |= TM_HIT_BAD_ID;
-        code = TM_BOUNDARY;
-    }
-    if (code != TM_BOUNDARY) {
-        const int32_t c = (int32_t)(code & ~TM_CFACE_FLAG);
-        const int4 r0 = __ldg(mv.cface + 2 * c);
-        const int4 r1 = __ldg(mv.cface + 2 * c + 1);  // vertex ids validated by the host build
-        const float4 a = __ldg(mv.pts + r1.x), b = __ldg(mv.pts + r1.y), d = __ldg(mv.pts + r1.z);
-        float th, u, v;
-        if (MODE == FP64) {
-            const float4 h = mt_hit_fp64(w0, w1, a, b, d);
-            th = h.x; u = h.y; v = h.z;
-        } else {
-            float cond;
-            mt_hit<float>(w0, w1, a, b, d, th, u, v, cond);
-            if (MODE == FP32G && !(cond <= kFinalCond)) {
-                const float4 h = mt_hit_fp64(w0, w1, a, b, d);
-                th = h.x; u = h.y; v = h.z;
-                flags |= TM_HIT_FINAL_FP64;
-            }
-        }
-        if (th <= w1.w) {
-            tri = r0.x;
-            cf = c;
-            t = th;
-            b1 = u;
-            b2 = v;
-            if (r0.y != tet) flags |= TM_HIT_SIDE_NEG;
-        }
-    }
-    __stcs(reinterpret_cast<int4 *>(hp), make_int4(tri, __float_as_int(t), __float_as_int(b1),
-                                                   __float_as_int(b2)));
-    __stcs(reinterpret_cast<int4 *>(hp) + 1, make_int4(tet, cf, (int)steps, (int)flags));
-}
-
-// Once per ray and with only value arguments: out of line by default.
-#ifdef TM_FINISH_INLINE
-#define TM_FINISH_ATTR __forceinline__
-#else
-#define TM_FINISH_ATTR __noinline__
-#endif
-
-template <int MODE>
-__device__ TM_FINISH_ATTR void finish_ray(const MeshView mv, const tm_ray *rp, tm_hit *hp,
-                                          uint32_t code, int32_t tet, uint32_t steps,
-                                          uint32_t flags) {
-    finish<MODE>(mv, rp, hp, code, tet, steps, flags);
+__device__ __forceinline__ int64_t ray_count(const PhaseParams &P) {
+    return P.n_dev ? min(P.n_cap, *P.n_dev) : P.n_cap;
 }
 
 // Rare start fallback: the origin lies on the boundary of the start tet and
@@ -160,44 +130,21 @@ __device__ __noinline__ int32_t search_start(const MeshView mv, const tm_ray *rp
     return -1;
 }
 
-template <class R, bool BOUNDED> struct Depth {
-    __device__ __forceinline__ void init(R, R, R, R, R, R, float) {}
-    __device__ __forceinline__ void set(int, const float4 &) {}
-    __device__ __forceinline__ bool beyond() const { return false; }
-};
-template <class R> struct Depth<R, true> {
-    R dx, dy, dz, dod, zmax, z0, z1, z2;
-    __device__ __forceinline__ void init(R ox, R oy, R oz, R x, R y, R z, float tmax) {
-        dx = x; dy = y; dz = z;
-        dod = rfma(dz, oz, rfma(dy, oy, rmul(dx, ox)));
-        zmax = R(tmax) * rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
-    }
-    __device__ __forceinline__ R depth(const float4 &p) const {
-        return rfma(dz, R(p.z), rfma(dy, R(p.y), rmul(dx, R(p.x)))) - dod;
-    }
-    __device__ __forceinline__ void set(int slot, const float4 &p) {
-        const R z = depth(p);
-        if (slot == 0) z0 = z; else if (slot == 1) z1 = z; else z2 = z;
-    }
-    // the entry face of the next tet lies entirely beyond t_max
-    __device__ __forceinline__ bool beyond() const { return fmin(z0, fmin(z1, z2)) > zmax; }
-};
-
-// Starts the ray at rp: basis, projected origin, and the exit face of its
-// start tet (interior start) or of the tet behind its restart face.  Returns
-// true when the walk continues in S.tet; otherwise the hit is written.
-template <int MODE, bool BOUNDED>
-__device__ __forceinline__ bool start_ray(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
-                                          WalkState<typename RealOf<MODE>::T> &S,
-                                          Basis<typename RealOf<MODE>::T> &B,
-                                          Depth<typename RealOf<MODE>::T, BOUNDED> &Z,
-                                          SignCtx &sc, uint32_t &steps) {
+// Phase 1 for one ray.
+template <int MODE>
+__device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
+                                          float tau_rel) {
     typedef typename RealOf<MODE>::T R;
     const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(rp));
     const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(rp) + 1);
-    B = make_basis<R>(R(w1.x), R(w1.y), R(w1.z), R(w0.x), R(w0.y), R(w0.z));
+    const Basis<R> B = make_basis<R>(R(w1.x), R(w1.y), R(w1.z), R(w0.x), R(w0.y), R(w0.z));
+    SignCtx sc;
+    sc.ray = rp;
+    sc.pts = mv.pts;
+    sc.tau = tau_rel * mv.extent;
     sc.flags = 0;
-    steps = 0;
+    WalkState<R> S;
+    uint32_t steps = 0;
     const int32_t start = __float_as_int(w0.w);
     uint32_t next = TM_BOUNDARY;
     int32_t T = -1;
@@ -247,42 +194,232 @@ __device__ __forceinline__ bool start_ray(const MeshView &mv, const tm_ray *rp, 
             }
         }
     }
-    if (!ok) {
-        finish_ray<MODE>(mv, rp, hp, TM_BOUNDARY, T, steps, sc.flags | TM_HIT_BAD_START);
-        return false;
-    }
-    if (next & TM_CFACE_FLAG) {
-        finish_ray<MODE>(mv, rp, hp, next, S.prev, steps, sc.flags);
-        return false;
-    }
-    S.tet = (int32_t)next;
-    if (BOUNDED) {
-        Z.init(R(w0.x), R(w0.y), R(w0.z), R(w1.x), R(w1.y), R(w1.z), w1.w);
-        Z.set(0, __ldg(mv.pts + S.i0));
-        Z.set(1, __ldg(mv.pts + S.i1));
-        Z.set(2, __ldg(mv.pts + S.i2));
-        if (Z.beyond()) {
-            finish_ray<MODE>(mv, rp, hp, TM_BOUNDARY, S.prev, steps, sc.flags);
-            return false;
-        }
-    }
-    return true;
+    if (!ok)
+        put_end(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_START);
+    else if (next & TM_CFACE_FLAG)
+        put_end(hp, S.prev, next, steps, sc.flags);
+    else
+        put_record(hp, 0, (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
 }
 
-// Register budget per thread of the walk (FP32 arms; the FP64 arm needs
+template <int MODE, bool MULTI>
+__global__ void __launch_bounds__(256)
+start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
+             tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
+             const __grid_constant__ PhaseParams P) {
+    const int64_t n = ray_count(P);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (MULTI) {
+            const Slot s = find_slot(descs, n_meshes, (unsigned long long)r);
+            const BatchDesc &D = descs[s.m];
+            start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel);
+        } else {
+            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel);
+        }
+    }
+}
+
+// In guard mode the float32 ray-triangle test is redone in double precision
+// when its condition estimate (see mt_hit) exceeds kFinalCond, i.e. when the
+// float32 t could be off by more than about 2e-6 relative.
+constexpr float kFinalCond = 32.f;
+
+// Phase 3 for one ray: the hit (or miss) from the end record.
+template <int MODE>
+__device__ __forceinline__ void finish_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp) {
+    const int4 e0 = __ldcs(reinterpret_cast<const int4 *>(hp));
+    const int4 e1 = __ldcs(reinterpret_cast<const int4 *>(hp) + 1);
+    const int32_t tet = e0.y;
+    uint32_t code = (uint32_t)e0.z;
+    const uint32_t steps = (uint32_t)e1.z;
+    uint32_t flags = (uint32_t)e1.w;
+    if (e0.x != 1) {  // the walk never ended this ray (cannot happen for a completed launch)
+        code = TM_BOUNDARY;
+        flags |= TM_HIT_BAD_ID;
+    }
+    int32_t tri = -1, cf = -1;
+    float t = __int_as_float(0x7f800000), b1 = 0.f, b2 = 0.f;
+    if (code != TM_BOUNDARY && (int32_t)(code & ~TM_CFACE_FLAG) >= mv.nc) {
+        flags |= TM_HIT_BAD_ID;
+        code = TM_BOUNDARY;
+    }
+    if (code != TM_BOUNDARY) {
+        const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
+        const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
+        const int32_t c = (int32_t)(code & ~TM_CFACE_FLAG);
+        const int4 r0 = __ldg(mv.cface + 2 * c);
+        const int4 r1 = __ldg(mv.cface + 2 * c + 1);  // vertex ids validated by the host build
+        const float4 a = __ldg(mv.pts + r1.x), b = __ldg(mv.pts + r1.y), d = __ldg(mv.pts + r1.z);
+        float th, u, v;
+        if (MODE == FP64) {
+            double td, ud, vd, cd;
+            mt_hit<double>(w0, w1, a, b, d, td, ud, vd, cd);
+            th = (float)td; u = (float)ud; v = (float)vd;
+        } else {
+            float cond;
+            mt_hit<float>(w0, w1, a, b, d, th, u, v, cond);
+            if (MODE == FP32G && !(cond <= kFinalCond)) {
+                double td, ud, vd, cd;
+                mt_hit<double>(w0, w1, a, b, d, td, ud, vd, cd);
+                th = (float)td; u = (float)ud; v = (float)vd;
+                flags |= TM_HIT_FINAL_FP64;
+            }
+        }
+        if (th <= w1.w) {
+            tri = r0.x;
+            cf = c;
+            t = th;
+            b1 = u;
+            b2 = v;
+            if (r0.y != tet) flags |= TM_HIT_SIDE_NEG;
+        }
+    }
+    __stcs(reinterpret_cast<int4 *>(hp), make_int4(tri, __float_as_int(t), __float_as_int(b1),
+                                                   __float_as_int(b2)));
+    __stcs(reinterpret_cast<int4 *>(hp) + 1, make_int4(tet, cf, (int)steps, (int)flags));
+}
+
+template <int MODE, bool MULTI>
+__global__ void __launch_bounds__(256)
+finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
+              tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
+              const __grid_constant__ PhaseParams P) {
+    const int64_t n = ray_count(P);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (MULTI) {
+            const Slot s = find_slot(descs, n_meshes, (unsigned long long)r);
+            const BatchDesc &D = descs[s.m];
+            finish_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local);
+        } else {
+            finish_one<MODE>(mv0, rays0 + r, hits0 + r);
+        }
+    }
+}
+
+template <class R, bool BOUNDED> struct Depth {
+    __device__ __forceinline__ void init(const float4 &, const float4 &) {}
+    __device__ __forceinline__ void set(int, const float4 &) {}
+    __device__ __forceinline__ bool beyond() const { return false; }
+};
+template <class R> struct Depth<R, true> {
+    R dx, dy, dz, dod, zmax, z0, z1, z2;
+    __device__ __forceinline__ void init(const float4 &w0, const float4 &w1) {
+        dx = w1.x; dy = w1.y; dz = w1.z;
+        dod = rfma(dz, R(w0.z), rfma(dy, R(w0.y), rmul(dx, R(w0.x))));
+        zmax = R(w1.w) * rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
+    }
+    __device__ __forceinline__ R depth(const float4 &p) const {
+        return rfma(dz, R(p.z), rfma(dy, R(p.y), rmul(dx, R(p.x)))) - dod;
+    }
+    __device__ __forceinline__ void set(int slot, const float4 &p) {
+        const R z = depth(p);
+        if (slot == 0) z0 = z; else if (slot == 1) z1 = z; else z2 = z;
+    }
+    // the entry face of the next tet lies entirely beyond t_max
+    __device__ __forceinline__ bool beyond() const { return fmin(z0, fmin(z1, z2)) > zmax; }
+};
+
+struct WalkParams {
+    int64_t n_cap;
+    const int64_t *n_dev;
+    unsigned long long *cursor;  // the walk's ray counter
+    uint32_t max_steps;
+    float tau_rel;
+    int refill;
+    int batch_steps;
+};
+
+// Guard mode: one step of a parked ray, with the double-precision re-test of
+// the sign tests that fell within the threshold (the float32 walk left it
+// undecided).  Reads the walk record from the hit slot and writes back the
+// record of the next tet, or the end record.  Out of line: no walk state is
+// live across the call, so the walk loop keeps its small register budget.
+template <bool BOUNDED>
+__device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp, tm_hit *hp,
+                                            float tau_rel, uint32_t max_steps) {
+    typedef float R;
+    const int4 a = __ldcg(reinterpret_cast<const int4 *>(hp));
+    const int4 b = __ldcg(reinterpret_cast<const int4 *>(hp) + 1);
+    WalkState<R> S;
+    S.tet = a.y;
+    S.prev = a.z;
+    S.i0 = a.w;
+    S.i1 = b.x;
+    S.i2 = b.y;
+    uint32_t steps = (uint32_t)b.z;
+    SignCtx sc;
+    sc.ray = rp;
+    sc.pts = mv.pts;
+    sc.tau = tau_rel * mv.extent;
+    sc.flags = (uint32_t)b.w | TM_HIT_SLOW_PASS;
+    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
+    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
+    const Basis<R> B = make_basis<R>(w1.x, w1.y, w1.z, w0.x, w0.y, w0.z);
+    const float4 x0 = __ldg(mv.pts + S.i0), x1 = __ldg(mv.pts + S.i1), x2 = __ldg(mv.pts + S.i2);
+    S.p0 = B.project(x0.x, x0.y, x0.z);
+    S.p1 = B.project(x1.x, x1.y, x1.z);
+    S.p2 = B.project(x2.x, x2.y, x2.z);
+    S.m0 = guard_mag(S.p0, sc.tau);
+    S.m1 = guard_mag(S.p1, sc.tau);
+    S.m2 = guard_mag(S.p2, sc.tau);
+    const int4 rec = __ldg(mv.tet16 + S.tet);
+    const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.x;
+    if ((uint32_t)i3 >= (uint32_t)mv.np) {
+        put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
+        return;
+    }
+    const float4 x = __ldg(mv.pts + i3);
+    const P2<R> p3 = B.project(x.x, x.y, x.z);
+    const float m3 = guard_mag(p3, sc.tau);
+    const int e = exit_slot_bits(step_signs<FP32G, false, true>(S, p3, i3, m3, sc));
+    const int ra = (S.i0 < i3) + (S.i1 < i3) + (S.i2 < i3);
+    const int32_t ie = e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2);
+    const int rb = (S.i0 < ie) + (S.i1 < ie) + (S.i2 < ie) + (i3 < ie);
+    const uint32_t nxa = ra == 0 ? rec.y : (ra == 1 ? rec.z : (ra == 2 ? rec.w : 0));
+    const uint32_t nxb = rb == 0 ? rec.y : (rb == 1 ? rec.z : (rb == 2 ? rec.w : 0));
+    const uint32_t next = (uint32_t)S.prev ^ nxa ^ nxb;
+    float4 xf[3] = {x0, x1, x2};
+    if (e == 0) S.i0 = i3; else if (e == 1) S.i1 = i3; else S.i2 = i3;
+    xf[e] = x;
+    ++steps;
+    if (next & TM_CFACE_FLAG) {
+        put_end(hp, S.tet, next, steps, sc.flags);
+    } else if (next >= (uint32_t)mv.nt) {
+        put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
+    } else if (steps >= max_steps) {
+        put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_STEP_LIMIT);
+    } else {
+        if (BOUNDED) {
+            Depth<R, true> Z;
+            Z.init(w0, w1);
+            Z.set(0, xf[0]);
+            Z.set(1, xf[1]);
+            Z.set(2, xf[2]);
+            if (Z.beyond()) {
+                put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags);
+                return;
+            }
+        }
+        put_record(hp, 0, (int32_t)next, (uint32_t)S.tet, S.i0, S.i1, S.i2, steps, sc.flags);
+    }
+}
+
+// Register budget per thread of the walk (float32; the FP64 arm keeps
 // double-width state).  Set by measurement on GB300.
-#ifndef TM_TRACE_MAXREG
-#define TM_TRACE_MAXREG 64
+#ifndef TM_WALK_MAXREG
+#define TM_WALK_MAXREG 48
 #endif
-#ifndef TM_TRACE_MAXREG_FP64
-#define TM_TRACE_MAXREG_FP64 80
+#ifndef TM_WALK_MAXREG_FP64
+#define TM_WALK_MAXREG_FP64 72
 #endif
 
 template <int MODE, bool BOUNDED, bool MULTI>
-__global__ void __maxnreg__(MODE == FP64 ? TM_TRACE_MAXREG_FP64 : TM_TRACE_MAXREG)
-trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
-             tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
-             const __grid_constant__ TraceParams P) {
+__global__ void __maxnreg__(MODE == FP64 ? TM_WALK_MAXREG_FP64 : TM_WALK_MAXREG)
+walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
+            tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
+            const __grid_constant__ WalkParams P) {
     typedef typename RealOf<MODE>::T R;
     extern __shared__ BatchDesc sdesc[];
     if (MULTI) {
@@ -293,8 +430,9 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
     int64_t n = P.n_cap;
     if (P.n_dev) n = min(n, *P.n_dev);
 
-    bool active = false, pool_empty = false;
-    int32_t m = 0, local = 0;
+    bool active = false, parked = false, pool_empty = false;
+    int32_t m = 0;
+    tm_hit *hp = nullptr;
     const int4 *tet16 = mv0.tet16;
     const float4 *pts = mv0.pts;
     WalkState<R> S;
@@ -308,7 +446,14 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
     uint32_t steps = 0;
 
     for (;;) {
-        const unsigned idle = __ballot_sync(kFull, !active);
+        bool load = false;
+        if (MODE == FP32G && parked) {
+            // re-decide the step this lane parked, then go on from its new record
+            resolve_parked<BOUNDED>(MULTI ? sdesc[m].mesh : mv0, sc.ray, hp, P.tau_rel, P.max_steps);
+            parked = false;
+            load = true;
+        }
+        const unsigned idle = __ballot_sync(kFull, !active && !load);
         const int n_idle = __popc(idle);
         if (!pool_empty && n_idle >= P.refill) {
             unsigned long long base = 0;
@@ -316,17 +461,12 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
             base = __shfl_sync(kFull, base, 0);
             if (base + (unsigned long long)n_idle >= (unsigned long long)n) pool_empty = true;
             const unsigned long long r = base + __popc(idle & ((1u << lane) - 1u));
-            if (!active && r < (unsigned long long)n) {
-                tm_hit *hp;
+            if (!active && !load && r < (unsigned long long)n) {
+                int32_t local;
                 if (MULTI) {
-                    int lo = 0, hi = n_meshes - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if ((unsigned long long)sdesc[mid].offset <= r) lo = mid; else hi = mid - 1;
-                    }
-                    m = lo;
-                    local = (int32_t)(r - (unsigned long long)sdesc[m].offset);
-                    if (sdesc[m].perm) local = sdesc[m].perm[local];
+                    const Slot s = find_slot(sdesc, n_meshes, r);
+                    m = s.m;
+                    local = sdesc[m].perm ? sdesc[m].perm[s.local] : s.local;
                     tet16 = sdesc[m].mesh.tet16;
                     pts = sdesc[m].mesh.pts;
                     sc.ray = sdesc[m].rays + local;
@@ -338,11 +478,46 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
                     sc.ray = rays0 + local;
                     hp = hits0 + local;
                 }
-                active = start_ray<MODE, BOUNDED>(MULTI ? sdesc[m].mesh : mv0, sc.ray, hp, S, B, Z,
-                                                  sc, steps);
+                load = true;
             }
         }
-        if (!__any_sync(kFull, active)) {
+        if (load) {
+            const int4 a = __ldcg(reinterpret_cast<const int4 *>(hp));
+            if (a.x == 0) {
+                const int4 b = __ldcg(reinterpret_cast<const int4 *>(hp) + 1);
+                S.tet = a.y;
+                S.prev = a.z;
+                S.i0 = a.w;
+                S.i1 = b.x;
+                S.i2 = b.y;
+                steps = (uint32_t)b.z;
+                sc.flags = (uint32_t)b.w;
+                const float4 w0 = __ldg(reinterpret_cast<const float4 *>(sc.ray));
+                const float4 w1 = __ldg(reinterpret_cast<const float4 *>(sc.ray) + 1);
+                B = make_basis<R>(R(w1.x), R(w1.y), R(w1.z), R(w0.x), R(w0.y), R(w0.z));
+                const float4 x0 = __ldg(pts + S.i0), x1 = __ldg(pts + S.i1), x2 = __ldg(pts + S.i2);
+                S.p0 = B.project(R(x0.x), R(x0.y), R(x0.z));
+                S.p1 = B.project(R(x1.x), R(x1.y), R(x1.z));
+                S.p2 = B.project(R(x2.x), R(x2.y), R(x2.z));
+                if (MODE == FP32G) {
+                    S.m0 = guard_mag(S.p0, sc.tau);
+                    S.m1 = guard_mag(S.p1, sc.tau);
+                    S.m2 = guard_mag(S.p2, sc.tau);
+                }
+                active = true;
+                if (BOUNDED) {
+                    Z.init(w0, w1);
+                    Z.set(0, x0);
+                    Z.set(1, x1);
+                    Z.set(2, x2);
+                    if (Z.beyond()) {
+                        put_end(hp, S.prev, TM_BOUNDARY, steps, sc.flags);
+                        active = false;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(kFull, active || parked)) {
             if (pool_empty) break;
             continue;
         }
@@ -361,7 +536,16 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
                 const float4 x = __ldg(pts + i3);
                 const P2<R> p3 = B.project(R(x.x), R(x.y), R(x.z));
                 const float m3 = MODE == FP32G ? guard_mag(p3, sc.tau) : 0.f;
-                const int e = exit_slot_bits(step_signs<MODE>(S, p3, i3, m3, sc));
+                const uint32_t sig = step_signs<MODE, MODE == FP32G, false>(S, p3, i3, m3, sc);
+                if (MODE == FP32G && sig == kParked) {
+                    // undecided in float32: park the ray; the lane re-decides this
+                    // step out of line at its next refill
+                    put_record(hp, 2, S.tet, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
+                    active = false;
+                    parked = true;
+                    continue;
+                }
+                const int e = exit_slot_bits(sig);
                 const int ra = (S.i0 < i3) + (S.i1 < i3) + (S.i2 < i3);
                 const int32_t ie = e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2);
                 const int rb = (S.i0 < ie) + (S.i1 < ie) + (S.i2 < ie) + (i3 < ie);
@@ -393,9 +577,7 @@ trace_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
                 }
             }
             if (done) {
-                finish_ray<MODE>(MULTI ? sdesc[m].mesh : mv0, sc.ray,
-                                 MULTI ? sdesc[m].hits + local : hits0 + local, code, S.tet, steps,
-                                 sc.flags);
+                put_end(hp, S.tet, code, steps, sc.flags);
                 active = false;
             }
         }
@@ -408,21 +590,6 @@ using namespace tmk;
 
 namespace {
 
-template <int MODE, bool BOUNDED, bool MULTI>
-cudaError_t launch_one(const MeshView &mv, const tm_ray *rays, tm_hit *hits, const BatchDesc *descs,
-                       int n_meshes, const TraceParams &P, int block, int grid, cudaStream_t s) {
-    const size_t smem = MULTI ? sizeof(BatchDesc) * (size_t)n_meshes : 0;
-    trace_kernel<MODE, BOUNDED, MULTI><<<grid, block, smem, s>>>(mv, rays, hits, descs, n_meshes, P);
-    return cudaGetLastError();
-}
-
-template <int MODE, bool BOUNDED, bool MULTI>
-int occupancy(int block, size_t smem) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<MODE, BOUNDED, MULTI>, block, smem);
-    return nb;
-}
-
 int sm_count_cached() {
     static int count = 0;
     if (count == 0) {
@@ -434,23 +601,54 @@ int sm_count_cached() {
     return count;
 }
 
+template <int MODE, bool BOUNDED, bool MULTI>
+int walk_occupancy(int block, size_t smem) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<MODE, BOUNDED, MULTI>, block, smem);
+    return nb;
+}
+
 template <bool BOUNDED, bool MULTI>
 int occupancy_mode(int mode, int block, size_t smem) {
     switch (mode) {
-        case FP32G: return occupancy<FP32G, BOUNDED, MULTI>(block, smem);
-        case FP32: return occupancy<FP32, BOUNDED, MULTI>(block, smem);
-        default: return occupancy<FP64, BOUNDED, MULTI>(block, smem);
+        case FP32G: return walk_occupancy<FP32G, BOUNDED, MULTI>(block, smem);
+        case FP32: return walk_occupancy<FP32, BOUNDED, MULTI>(block, smem);
+        default: return walk_occupancy<FP64, BOUNDED, MULTI>(block, smem);
     }
+}
+
+// Launches start, walk and finish for one mode.
+template <int MODE, bool BOUNDED, bool MULTI>
+cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, const BatchDesc *descs,
+                          int n_meshes, const WalkParams &W, int block, int walk_grid,
+                          const cudaEvent_t *ev, cudaStream_t s) {
+    PhaseParams P;
+    P.n_cap = W.n_cap;
+    P.n_dev = W.n_dev;
+    P.tau_rel = W.tau_rel;
+    const int sms = sm_count_cached();
+    int64_t g = (W.n_cap + 255) / 256;
+    const int64_t gmax = (int64_t)sms * 16;
+    if (g > gmax) g = gmax;
+    if (ev && ev[0]) cudaEventRecord(ev[0], s);
+    start_kernel<MODE, MULTI><<<(int)g, 256, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
+    if (ev && ev[1]) cudaEventRecord(ev[1], s);
+    const size_t smem = MULTI ? sizeof(BatchDesc) * (size_t)n_meshes : 0;
+    walk_kernel<MODE, BOUNDED, MULTI><<<walk_grid, block, smem, s>>>(mv, rays, hits, descs, n_meshes, W);
+    if (ev && ev[2]) cudaEventRecord(ev[2], s);
+    finish_kernel<MODE, MULTI><<<(int)g, 256, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
+    if (ev && ev[3]) cudaEventRecord(ev[3], s);
+    return cudaGetLastError();
 }
 
 template <bool BOUNDED, bool MULTI>
 cudaError_t dispatch(int mode, const MeshView &mv, const tm_ray *rays, tm_hit *hits,
-                     const BatchDesc *descs, int n_meshes, const TraceParams &P, int block, int grid,
-                     cudaStream_t s) {
+                     const BatchDesc *descs, int n_meshes, const WalkParams &W, int block, int grid,
+                     const cudaEvent_t *ev, cudaStream_t s) {
     switch (mode) {
-        case FP32G: return launch_one<FP32G, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, P, block, grid, s);
-        case FP32: return launch_one<FP32, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, P, block, grid, s);
-        default: return launch_one<FP64, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, P, block, grid, s);
+        case FP32G: return launch_phases<FP32G, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+        case FP32: return launch_phases<FP32, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+        default: return launch_phases<FP64, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
     }
 }
 
@@ -478,6 +676,7 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.batch_steps = (o && o->batch_steps) ? o->batch_steps : 16;
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
+    for (int i = 0; i < 4; ++i) c.events[i] = o ? (cudaEvent_t)o->phase_events[i] : nullptr;
     return c;
 }
 
@@ -492,33 +691,32 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
     if (!valid_config(cfg)) return TM_ERR_ARG;
     if (n == 0) return TM_OK;
     if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
-    unsigned long long *cursor = nullptr;
+    unsigned long long *cursor = nullptr;  // the walk's ray counter
     TM_CUDA(cudaMallocAsync((void **)&cursor, sizeof(unsigned long long), s));
     TM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
-    TraceParams P;
-    P.n_cap = n;
-    P.n_dev = n_dev;
-    P.cursor = cursor;
-    P.max_steps = cfg.max_steps;
-    P.tau_rel = cfg.tau;
-    P.refill = cfg.refill;
-    P.batch_steps = cfg.batch_steps;
+    WalkParams W;
+    W.n_cap = n;
+    W.n_dev = n_dev;
+    W.cursor = cursor;
+    W.max_steps = cfg.max_steps;
+    W.tau_rel = cfg.tau;
+    W.refill = cfg.refill;
+    W.batch_steps = cfg.batch_steps;
     int sms = 0;
-    const bool bnd = cfg.bounded;
-    const int mode = cfg.mode;
-    int per_sm = max_persistent_ctas(mode, false, bnd, cfg.block, &sms);
+    int per_sm = max_persistent_ctas(cfg.mode, false, cfg.bounded, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
     int64_t grid = (int64_t)per_sm * sms;
     const int64_t need = (n + cfg.block - 1) / cfg.block;
     if (!n_dev && grid > need) grid = need;
-    cudaError_t e = bnd ? dispatch<true, false>(mode, mv, rays, hits, nullptr, 0, P, cfg.block, (int)grid, s)
-                        : dispatch<false, false>(mode, mv, rays, hits, nullptr, 0, P, cfg.block, (int)grid, s);
+    cudaError_t e = cfg.bounded
+        ? dispatch<true, false>(cfg.mode, mv, rays, hits, nullptr, 0, W, cfg.block, (int)grid, cfg.events, s)
+        : dispatch<false, false>(cfg.mode, mv, rays, hits, nullptr, 0, W, cfg.block, (int)grid, cfg.events, s);
     if (e != cudaSuccess) {
-        tm_set_error("trace_kernel launch", e);
+        tm_set_error("trace launch", e);
         cudaFreeAsync(cursor, s);
         return TM_ERR_CUDA;
     }
-    tm_count_launches(1);
+    tm_count_launches(3);
     TM_CUDA(cudaFreeAsync(cursor, s));
     return TM_OK;
 }
@@ -528,29 +726,28 @@ tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t t
                              bool count) {
     if (!valid_config(cfg) || n_meshes < 1 || n_meshes > kMaxBatch) return TM_ERR_ARG;
     if (total == 0) return TM_OK;
-    TraceParams P;
-    P.n_cap = total;
-    P.n_dev = nullptr;
-    P.cursor = cursor;
-    P.max_steps = cfg.max_steps;
-    P.tau_rel = cfg.tau;
-    P.refill = cfg.refill;
-    P.batch_steps = cfg.batch_steps;
+    WalkParams W;
+    W.n_cap = total;
+    W.n_dev = nullptr;
+    W.cursor = cursor;
+    W.max_steps = cfg.max_steps;
+    W.tau_rel = cfg.tau;
+    W.refill = cfg.refill;
+    W.batch_steps = cfg.batch_steps;
     int sms = 0;
-    const int mode = cfg.mode;
-    int per_sm = max_persistent_ctas(mode, true, false, cfg.block, &sms);
+    int per_sm = max_persistent_ctas(cfg.mode, true, false, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
     int64_t grid = (int64_t)per_sm * sms;
     const int64_t need = (total + cfg.block - 1) / cfg.block;
     if (grid > need) grid = need;
     TM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
     MeshView dummy{};
-    cudaError_t e = dispatch<false, true>(mode, dummy, nullptr, nullptr, descs_dev, n_meshes, P,
-                                          cfg.block, (int)grid, s);
+    cudaError_t e = dispatch<false, true>(cfg.mode, dummy, nullptr, nullptr, descs_dev, n_meshes, W,
+                                          cfg.block, (int)grid, nullptr, s);
     if (e != cudaSuccess) {
-        tm_set_error("trace_kernel (batch) launch", e);
+        tm_set_error("trace (batch) launch", e);
         return TM_ERR_CUDA;
     }
-    if (count) tm_count_launches(1);
+    if (count) tm_count_launches(3);
     return TM_OK;
 }

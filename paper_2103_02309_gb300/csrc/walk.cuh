@@ -283,9 +283,9 @@ __device__ __noinline__ static int2 step3d(const MeshView &mv, const tm_ray *ray
 // projections of the two points (ties broken by vertex ids).  Out of line:
 // the rare path.  Returns the three signs in bits 0..2 and TM_HIT_GUARD /
 // TM_HIT_TIE in bits 8 and up.
-__device__ __noinline__ static uint32_t guard_signs(const tm_ray *ray, const float4 *pts, float d0,
-                                                    float d1, float d2, float t0, float t1, float t2,
-                                                    int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
+__device__ __forceinline__ uint32_t guard_signs_impl(const tm_ray *ray, const float4 *pts, float d0,
+                                                     float d1, float d2, float t0, float t1, float t2,
+                                                     int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
     const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
     const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
     const Basis<double> B = make_basis<double>(w1.x, w1.y, w1.z, w0.x, w0.y, w0.z);
@@ -313,10 +313,20 @@ __device__ __noinline__ static uint32_t guard_signs(const tm_ray *ray, const flo
     }
     return bits | (flags << 8);
 }
+__device__ __noinline__ static uint32_t guard_signs(const tm_ray *ray, const float4 *pts, float d0,
+                                                    float d1, float d2, float t0, float t1, float t2,
+                                                    int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
+    return guard_signs_impl(ray, pts, d0, d1, d2, t0, t1, t2, i0, i1, i2, i3);
+}
 
 // The three sign tests of one step, det(p3, p_k) > 0 for the entry-face
-// slots k = 0, 1, 2 (bit k), with the same decision rule as pos().
-template <int MODE, class R>
+// slots k = 0, 1, 2 (bit k), with the same decision rule as pos().  In guard
+// mode with PARK, a step with an ambiguous test is not decided: the function
+// returns kParked and the caller hands the ray to the slow pass; INLINE_GUARD
+// inlines the double-precision re-test instead of calling it.
+constexpr uint32_t kParked = 0xffffffffu;
+
+template <int MODE, bool PARK, bool INLINE_GUARD, class R>
 __device__ __forceinline__ uint32_t step_signs(const WalkState<R> &S, const P2<R> &p3, int32_t i3,
                                                float m3, SignCtx &c) {
     const R d0 = det2(p3, S.p0), d1 = det2(p3, S.p1), d2 = det2(p3, S.p2);
@@ -325,8 +335,10 @@ __device__ __forceinline__ uint32_t step_signs(const WalkState<R> &S, const P2<R
         const float t0 = fmaxf(m3, S.m0), t1 = fmaxf(m3, S.m1), t2 = fmaxf(m3, S.m2);
         const bool amb = !(fabsf((float)d0) > t0) | !(fabsf((float)d1) > t1) | !(fabsf((float)d2) > t2);
         if (amb) {
-            const uint32_t r = guard_signs(c.ray, c.pts, (float)d0, (float)d1, (float)d2, t0, t1, t2,
-                                           S.i0, S.i1, S.i2, i3);
+            if (PARK) return kParked;
+            const uint32_t r = INLINE_GUARD
+                ? guard_signs_impl(c.ray, c.pts, (float)d0, (float)d1, (float)d2, t0, t1, t2, S.i0, S.i1, S.i2, i3)
+                : guard_signs(c.ray, c.pts, (float)d0, (float)d1, (float)d2, t0, t1, t2, S.i0, S.i1, S.i2, i3);
             c.flags |= r >> 8;
             bits = r & 7u;
         }

@@ -29,6 +29,7 @@ HIT_FINAL_FP64 = 0x20
 HIT_RESTART_3D = 0x40
 HIT_BAD_ID = 0x80
 HIT_START_MOVED = 0x100
+HIT_SLOW_PASS = 0x200
 
 IDS_TET, IDS_POINT = 0, 1
 TO_INPUT, TO_INTERNAL = 0, 1
@@ -54,7 +55,9 @@ def _hptr(a: np.ndarray):
 
 
 def trace_opts(mode="fp32g", guard_tau=0.0, max_steps=0, block=0, refill=0, batch_steps=0,
-               ctas_per_sm=0, tmax_early_exit=False) -> N.TraceOpts:
+               ctas_per_sm=0, tmax_early_exit=False, phase_events=None) -> N.TraceOpts:
+    """Trace options; phase_events: four torch.cuda.Event (enable_timing) recorded
+    before the start phase, after it, after the walk and after the finish phase."""
     o = N.TraceOpts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.guard_tau = float(guard_tau)
@@ -64,6 +67,9 @@ def trace_opts(mode="fp32g", guard_tau=0.0, max_steps=0, block=0, refill=0, batc
     o.batch_steps = int(batch_steps)
     o.ctas_per_sm = int(ctas_per_sm)
     o.tmax_early_exit = 1 if tmax_early_exit else 0
+    if phase_events is not None:
+        for i, ev in enumerate(phase_events):
+            o.phase_events[i] = ev.cuda_event if ev is not None else None
     return o
 
 
