@@ -64,6 +64,15 @@ enum {
 
 enum { TM_ORDER_HILBERT = 0, TM_ORDER_INPUT = 1 };
 
+/* Tet record the walk reads (Sec. 3): Tet16 = VX and NX_j = N_j ^ N_3
+ * (16 B, the default, decoded with the previous tet, Alg. 7); Tet20 = VX and
+ * N_0..N_3 sorted by the ids of the vertices they sit across (20 B, Alg. 5;
+ * needs tm_build_opts.tet20), stored split (TM_FORMAT_TET20: a 16-B
+ * {VX, N0, N1, N2} array and a 4-B N3 array) or packed (TM_FORMAT_TET20_AOS:
+ * one int32[5] per tet at a 20-B stride); Tet32 = the full record V0..V3,
+ * N0..N3 (32 B, the mesh's cold records; Alg. 3 with VX = V0^V1^V2^V3). */
+enum { TM_FORMAT_TET16 = 0, TM_FORMAT_TET20 = 1, TM_FORMAT_TET32 = 2, TM_FORMAT_TET20_AOS = 3 };
+
 /* A ray, 32 bytes, two 16-byte words.
  *   start >= 0 : internal id of a tet that holds the origin (o).
  *   start <  0 : restart from a constrained face (Sec. 6): with
@@ -105,10 +114,13 @@ typedef struct {
                                      in a neighbouring tet that also holds it */
 #define TM_HIT_SLOW_PASS  0x200u  /* guard mode: at least one step had a sign test within the
                                      guard threshold and was re-decided out of line */
+#define TM_HIT_REACHED    0x400u  /* tm_trace_shadow: the walk reached the light's tet (no
+                                     constrained triangle in between); reported as a miss */
 
 typedef struct {
     int32_t order;           /* TM_ORDER_HILBERT (default) or TM_ORDER_INPUT */
     int32_t fix_orientation; /* nonzero: swap V2,V3 of tets with orient3d < 0 instead of failing */
+    int32_t tet20;           /* nonzero: also pack the Tet20 records, split and packed (40 B per tet) */
 } tm_build_opts;
 
 typedef struct {
@@ -124,6 +136,7 @@ typedef struct {
     void *phase_events[4];   /* optional cudaEvent_t handles recorded on the stream before the
                                 start phase, after it, after the walk and after the finish
                                 phase (tm_trace only); NULL entries are skipped */
+    int32_t format;          /* TM_FORMAT_*: the record the walk reads (batches: Tet16 only) */
 } tm_trace_opts;
 
 /* Mesh description returned by tm_mesh_info.  Device pointers are owned by
@@ -138,6 +151,9 @@ typedef struct {
     const void *points_dev;      /* float4[n_points] (x, y, z, 0) */
     const void *cold_dev;        /* int4[2*n_tets] (V0..V3 positively oriented, N0..N3) */
     const void *cface_dev;       /* int4[2*n_tris] (tri, tet+, tet-, 0, v0, v1, v2, 0) */
+    const void *tet20_dev;       /* int4[n_tets] (VX, N0, N1, N2), or NULL */
+    const void *tet20_n3_dev;    /* int32[n_tets] N3, or NULL */
+    const void *tet20_aos_dev;   /* int32[5*n_tets] (VX, N0, N1, N2, N3), or NULL */
     int64_t device_bytes;        /* bytes the mesh holds on the device */
 } tm_mesh_info;
 
@@ -172,6 +188,12 @@ tm_status tm_mesh_info_get(const tm_mesh *mesh, tm_mesh_info *info);
 tm_status tm_mesh_export(const tm_mesh *mesh, int32_t *tet16, int32_t *cold, float *points,
                          int32_t *cface, int32_t *point_perm, int32_t *tet_perm);
 
+/* Copies the Tet20 records (when built) into HOST buffers: vxn
+ * int32[n_tets*4] (VX, N0, N1, N2), n3 int32[n_tets] and aos int32[n_tets*5]
+ * (VX, N0..N3); NULL buffers are skipped.  TM_ERR_ARG if the mesh was built
+ * without them. */
+tm_status tm_mesh_export_tet20(const tm_mesh *mesh, int32_t *vxn, int32_t *n3, int32_t *aos);
+
 enum { TM_IDS_TET = 0, TM_IDS_POINT = 1 };
 enum { TM_TO_INPUT = 0, TM_TO_INTERNAL = 1 };
 /* Converts n ids (HOST arrays) between internal and input numbering.  Ids
@@ -203,6 +225,19 @@ tm_status tm_locate(const tm_mesh *mesh, const float *q, int64_t n, const int32_
 tm_status tm_trace(const tm_mesh *mesh, const tm_ray *rays, int64_t n, const int64_t *n_dev,
                    tm_hit *hits, const tm_trace_opts *opts, void *stream);
 
+/* Shadow rays toward a point light (Sec. 6): the walk of tm_trace, which
+ * also ends, as a miss flagged TM_HIT_REACHED, when it enters (or starts in)
+ * the tet light_tet that holds the light (internal id, e.g. from
+ * tm_locate).  A hit (tri >= 0) is the nearest constrained triangle between
+ * the origin and the light: the light is occluded.  Each ray's tmax should
+ * be its distance to the light (in units of |d|): a walk that passes the
+ * light's tet by rounding then still ends, as a miss without the flag,
+ * once its entry face lies beyond tmax (opts->tmax_early_exit is implied).
+ * Arguments as tm_trace; TM_ERR_ARG if light_tet is not a tet of the mesh. */
+tm_status tm_trace_shadow(const tm_mesh *mesh, const tm_ray *rays, int64_t n,
+                          const int64_t *n_dev, int32_t light_tet, tm_hit *hits,
+                          const tm_trace_opts *opts, void *stream);
+
 /* Pinhole camera of the synthetic workloads: eye, looking along +z, image x
  * along +x and image y (down) along -y; per pixel, with correctly rounded
  * float32 operations in this order (no fused multiply-add):
@@ -233,6 +268,38 @@ tm_status tm_gen_primary(const tm_camera *cam, const int32_t *start_dev, float t
 tm_status tm_gen_secondary(const tm_mesh *mesh, const tm_hit *hits, int64_t n,
                            const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                            tm_ray *rays_out, int64_t *count_dev, int32_t *src_out, void *stream);
+
+/* Shadow rays from hits (Sec. 6): for every hit i (tri >= 0) of the n
+ * DEVICE hits, one ray from the hit point x = a + b1 (b - a) + b2 (c - a)
+ * (triangle (a, b, c) in input order, float32) toward the point light
+ * (lx, ly, lz): d = (L - x) / |L - x|, tmax = |L - x|, restarted from the
+ * hit triangle into its side that faces the light (the + side when
+ * ((b - a) x (c - a)) . (L - a) >= 0).  Output, compaction, count and
+ * src_out as tm_gen_secondary (capacity n).  Trace them with
+ * tm_trace_shadow. */
+tm_status tm_gen_shadow(const tm_mesh *mesh, const tm_hit *hits, int64_t n, const int64_t *n_dev,
+                        float lx, float ly, float lz, tm_ray *rays_out, int64_t *count_dev,
+                        int32_t *src_out, void *stream);
+
+/* Reflection and refraction rays from hits (Sec. 6): for every hit i
+ * (tri >= 0) of the n DEVICE hits, made by ray i of rays_in, one ray from
+ * the hit point (as tm_gen_shadow) with unit direction
+ *   TM_SPECULAR_REFLECT: the mirror direction r = w + 2 c n_a, restarted
+ *     into the arrival side's tet;
+ *   TM_SPECULAR_REFRACT: the transmitted direction of Snell's law,
+ *     t = eta w + (eta c - sqrt(k)) n_a with k = 1 - eta^2 (1 - c^2),
+ *     restarted into the tet across the hit face; where k < 0 (total
+ *     internal reflection) the mirror direction instead,
+ * with w = d / |d| of the incoming ray, n_a the unit triangle normal turned
+ * toward the arrival side, c = -w . n_a (clamped at 0), and eta the ratio of
+ * refractive indices (arrival side over far side): ior for rays arriving
+ * from the - side, 1/ior from the + side (ior = index of the - side over
+ * that of the + side).  Output, compaction, count and src_out as
+ * tm_gen_secondary (capacity n), all rays with the given tmax. */
+enum { TM_SPECULAR_REFLECT = 0, TM_SPECULAR_REFRACT = 1 };
+tm_status tm_gen_specular(const tm_mesh *mesh, const tm_ray *rays_in, const tm_hit *hits,
+                          int64_t n, const int64_t *n_dev, int kind, float ior, float tmax,
+                          tm_ray *rays_out, int64_t *count_dev, int32_t *src_out, void *stream);
 
 /* The same as tm_gen_secondary, for callers that cannot allocate device
  * memory while they run (a renderer with a fixed memory budget, or code

@@ -113,3 +113,79 @@ def hit_side(ctet: np.ndarray, hit_tri: np.ndarray, hit_tet: np.ndarray) -> np.n
     ok = hit_tri >= 0
     side[ok] = np.where(ctet[hit_tri[ok], 0] == hit_tet[ok], 0, 1)
     return side
+
+
+def _hit_points(points, tris, hit_tri, hit_b1, hit_b2):
+    """Selected hit rows, triangle ids, hit points, first vertices and unnormalised normals (FP64)."""
+    P = np.asarray(points, dtype=np.float64)
+    tris = np.asarray(tris)
+    hit_tri = np.asarray(hit_tri)
+    sel = np.nonzero(hit_tri >= 0)[0]
+    c = hit_tri[sel].astype(np.int64)
+    v0, v1, v2 = P[tris[c, 0]], P[tris[c, 1]], P[tris[c, 2]]
+    b1 = np.asarray(hit_b1, dtype=np.float64)[sel]
+    b2 = np.asarray(hit_b2, dtype=np.float64)[sel]
+    x = (1.0 - b1 - b2)[:, None] * v0 + b1[:, None] * v1 + b2[:, None] * v2
+    nrm = np.cross(v1 - v0, v2 - v0)
+    return sel, c, x, v0, nrm
+
+
+def shadow_rays(points, tris, hit_tri, hit_b1, hit_b2, light):
+    """Shadow rays toward a point light (Sec. 6), one per hit (hit_tri >= 0).
+
+    From the hit point x toward L: d = (L - x)/|L - x|, tmax = |L - x|,
+    restarted from the hit triangle into the side that faces L (0, the +
+    side, when n . (L - v0) >= 0, n = (v1-v0) x (v2-v0); else 1).  Returns
+    o, d (float32 [M,3]), tmax (float32 [M]), entry = 2*tri + side (int32)
+    and src (int64, the hit index of each ray).
+    """
+    sel, c, x, v0, nrm = _hit_points(points, tris, hit_tri, hit_b1, hit_b2)
+    L = np.asarray(light, dtype=np.float64).reshape(1, 3)
+    side = np.where(np.einsum("ij,ij->i", nrm, L - v0) >= 0.0, 0, 1)
+    v = L - x
+    ln = np.linalg.norm(v, axis=1)
+    d = v / ln[:, None]
+    return (x.astype(np.float32), d.astype(np.float32), ln.astype(np.float32),
+            (2 * c + side).astype(np.int32), sel.astype(np.int64))
+
+
+def specular_rays(points, tris, hit_tri, hit_b1, hit_b2, hit_side, d_in, kind: str, ior: float,
+                  tmax: float):
+    """Reflection or refraction rays (Sec. 6), one per hit (hit_tri >= 0).
+
+    w = d_in / |d_in| (the incoming ray of each hit), n_a = the unit normal
+    turned toward the arrival side (hit_side 0: +, 1: -), c = max(0, -w.n_a).
+    Mirror direction r = w + 2 c n_a (Snell's law of reflection), restarted
+    on the arrival side.  Refraction (Snell's law, vector form): with eta the
+    ratio of refractive indices arrival side / far side (ior from the - side,
+    1/ior from the + side; ior = index of the - side over the + side) and
+    k = 1 - eta^2 (1 - c^2), the transmitted direction is
+    eta w + (eta c - sqrt(k)) n_a, restarted on the far side; k < 0 is total
+    internal reflection and gives the mirror direction.  Directions are
+    normalised; float64 throughout, one rounding to float32.  Returns o, d,
+    tmax, entry = 2*tri + side, src as shadow_rays, and k (float64).
+    """
+    sel, c, x, v0, nrm = _hit_points(points, tris, hit_tri, hit_b1, hit_b2)
+    side = np.asarray(hit_side)[sel].astype(np.int64)
+    n = nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+    na = np.where((side == 1)[:, None], -n, n)
+    w = np.asarray(d_in, dtype=np.float64)[sel]
+    w = w / np.linalg.norm(w, axis=1, keepdims=True)
+    cs = np.maximum(0.0, -np.einsum("ij,ij->i", w, na))
+    eta = np.where(side == 1, float(ior), 1.0 / float(ior))
+    k = 1.0 - eta * eta * (1.0 - cs * cs)
+    refl = w + (2.0 * cs)[:, None] * na
+    if kind == "refract":
+        ok = k >= 0.0
+        tr = eta[:, None] * w + (eta * cs - np.sqrt(np.maximum(k, 0.0)))[:, None] * na
+        d = np.where(ok[:, None], tr, refl)
+        out_side = np.where(ok, 1 - side, side)
+    elif kind == "reflect":
+        d = refl
+        out_side = side
+    else:
+        raise ValueError(kind)
+    d = d / np.linalg.norm(d, axis=1, keepdims=True)
+    tm = np.full(len(sel), tmax, dtype=np.float32)
+    return (x.astype(np.float32), d.astype(np.float32), tm, (2 * c + out_side).astype(np.int32),
+            sel.astype(np.int64), k)

@@ -41,20 +41,21 @@ f64 = ctypes.c_double
 
 
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("order", i32), ("fix_orientation", i32)]
+    _fields_ = [("order", i32), ("fix_orientation", i32), ("tet20", i32)]
 
 
 class TraceOpts(ctypes.Structure):
     _fields_ = [("mode", i32), ("guard_tau", f32), ("max_steps", ctypes.c_uint32), ("block", i32),
                 ("refill", i32), ("batch_steps", i32), ("ctas_per_sm", i32),
-                ("tmax_early_exit", i32), ("phase_events", P * 4)]
+                ("tmax_early_exit", i32), ("phase_events", P * 4), ("format", i32)]
 
 
 class MeshInfo(ctypes.Structure):
     _fields_ = [("n_points", i64), ("n_tets", i64), ("n_tris", i64), ("extent", f64),
                 ("bbox_lo", f32 * 3), ("bbox_hi", f32 * 3), ("source_tet", i32),
                 ("on_device", i32), ("tet16_dev", P), ("points_dev", P), ("cold_dev", P),
-                ("cface_dev", P), ("device_bytes", i64)]
+                ("cface_dev", P), ("tet20_dev", P), ("tet20_n3_dev", P), ("tet20_aos_dev", P),
+                ("device_bytes", i64)]
 
 
 class Camera(ctypes.Structure):
@@ -72,12 +73,16 @@ _SIGS = {
     "tm_destroy": ([P], None),
     "tm_mesh_info_get": ([P, ctypes.POINTER(MeshInfo)], ctypes.c_int),
     "tm_mesh_export": ([P, P, P, P, P, P, P], ctypes.c_int),
+    "tm_mesh_export_tet20": ([P, P, P, P], ctypes.c_int),
     "tm_map_ids": ([P, ctypes.c_int, ctypes.c_int, P, P, i64], ctypes.c_int),
     "tm_hilbert_keys": ([P, i64, ctypes.c_int, P], ctypes.c_int),
     "tm_locate": ([P, P, i64, P, i32, P, P], ctypes.c_int),
     "tm_trace": ([P, P, i64, P, P, ctypes.POINTER(TraceOpts), P], ctypes.c_int),
+    "tm_trace_shadow": ([P, P, i64, P, ctypes.c_int32, P, ctypes.POINTER(TraceOpts), P], ctypes.c_int),
     "tm_gen_primary": ([ctypes.POINTER(Camera), P, f32, P, P], ctypes.c_int),
     "tm_gen_secondary": ([P, P, i64, P, ctypes.c_int, f32, u64, P, P, P, P], ctypes.c_int),
+    "tm_gen_shadow": ([P, P, i64, P, f32, f32, f32, P, P, P, P], ctypes.c_int),
+    "tm_gen_specular": ([P, P, P, i64, P, ctypes.c_int, f32, f32, P, P, P, P], ctypes.c_int),
     "tm_gen_secondary_noalloc": ([P, P, i64, P, ctypes.c_int, f32, u64, P, P, P, P], ctypes.c_int),
     "tm_batch_create": ([P, ctypes.c_int, ctypes.POINTER(P)], ctypes.c_int),
     "tm_batch_set": ([P, P, P, P, ctypes.POINTER(TraceOpts), i32], ctypes.c_int),

@@ -118,6 +118,7 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
                         const int32_t *tris, int64_t nc, const tm_build_opts *opts, tm_mesh *m) {
     const int order = opts ? opts->order : TM_ORDER_HILBERT;
     const bool fix = opts ? opts->fix_orientation != 0 : false;
+    const bool want_t20 = opts ? opts->tet20 != 0 : false;
     if (order != TM_ORDER_HILBERT && order != TM_ORDER_INPUT) return TM_ERR_ARG;
     m->np = np;
     m->nt = nt;
@@ -308,6 +309,11 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
     }
     m->cold.resize((size_t)nt * 8);
     m->tet16.resize((size_t)nt * 4);
+    if (want_t20) {
+        m->t20.resize((size_t)nt * 4);
+        m->t20n3.resize((size_t)nt);
+        m->t20aos.resize((size_t)nt * 5);
+    }
 #pragma omp parallel for schedule(static)
     for (int64_t tn = 0; tn < nt; ++tn) {
         const int64_t t = m->tperm[(size_t)tn];
@@ -328,6 +334,15 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
         m->tet16[4 * tn + 1] = (int32_t)(NB[idx[0]] ^ n3);
         m->tet16[4 * tn + 2] = (int32_t)(NB[idx[1]] ^ n3);
         m->tet16[4 * tn + 3] = (int32_t)(NB[idx[2]] ^ n3);
+        if (want_t20) {
+            m->t20[4 * tn + 0] = m->tet16[4 * tn + 0];
+            m->t20[4 * tn + 1] = (int32_t)NB[idx[0]];
+            m->t20[4 * tn + 2] = (int32_t)NB[idx[1]];
+            m->t20[4 * tn + 3] = (int32_t)NB[idx[2]];
+            m->t20n3[tn] = (int32_t)n3;
+            for (int j = 0; j < 4; ++j) m->t20aos[5 * tn + j] = m->t20[4 * tn + j];
+            m->t20aos[5 * tn + 4] = (int32_t)n3;
+        }
     }
     m->cface.resize((size_t)nc * 8);
 #pragma omp parallel for schedule(static)
@@ -389,6 +404,17 @@ tm_status tm_upload(tm_mesh *m) {
         TM_CUDA(cudaMemcpy(m->d_cface, m->cface.data(), 2 * sizeof(int4) * (size_t)m->nc,
                            cudaMemcpyHostToDevice));
     m->device_bytes = (int64_t)(b_tet + b_pts + b_cold + b_cf);
+    if (!m->t20.empty()) {
+        TM_CUDA(cudaMalloc(&m->d_t20, sizeof(int4) * (size_t)m->nt));
+        TM_CUDA(cudaMalloc(&m->d_t20n3, sizeof(int32_t) * (size_t)m->nt));
+        TM_CUDA(cudaMemcpy(m->d_t20, m->t20.data(), sizeof(int4) * (size_t)m->nt, cudaMemcpyHostToDevice));
+        TM_CUDA(cudaMemcpy(m->d_t20n3, m->t20n3.data(), sizeof(int32_t) * (size_t)m->nt,
+                           cudaMemcpyHostToDevice));
+        TM_CUDA(cudaMalloc(&m->d_t20aos, 5 * sizeof(int32_t) * (size_t)m->nt));
+        TM_CUDA(cudaMemcpy(m->d_t20aos, m->t20aos.data(), 5 * sizeof(int32_t) * (size_t)m->nt,
+                           cudaMemcpyHostToDevice));
+        m->device_bytes += (int64_t)(40 * m->nt);
+    }
     m->on_device = true;
     // seed lattice: locate the centres of a kSeedGrid^3 lattice over the
     // bounding cube once, from the default source tet
@@ -433,6 +459,12 @@ void tm_free_device(tm_mesh *m) {
     cudaFree(m->d_cface);
     cudaFree(m->d_seeds);
     m->d_seeds = nullptr;
+    cudaFree(m->d_t20);
+    cudaFree(m->d_t20n3);
+    cudaFree(m->d_t20aos);
+    m->d_t20 = nullptr;
+    m->d_t20n3 = nullptr;
+    m->d_t20aos = nullptr;
     m->d_tet16 = nullptr;
     m->d_pts = nullptr;
     m->d_cold = nullptr;

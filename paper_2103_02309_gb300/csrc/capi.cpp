@@ -98,6 +98,9 @@ tm_status tm_mesh_info_get(const tm_mesh *m, tm_mesh_info *info) {
     info->points_dev = m->d_pts;
     info->cold_dev = m->d_cold;
     info->cface_dev = m->d_cface;
+    info->tet20_dev = m->d_t20;
+    info->tet20_n3_dev = m->d_t20n3;
+    info->tet20_aos_dev = m->d_t20aos;
     info->device_bytes = m->device_bytes;
     return TM_OK;
 }
@@ -111,6 +114,14 @@ tm_status tm_mesh_export(const tm_mesh *m, int32_t *tet16, int32_t *cold, float 
     if (cface && !m->cface.empty()) std::memcpy(cface, m->cface.data(), sizeof(int32_t) * m->cface.size());
     if (point_perm) std::memcpy(point_perm, m->pperm.data(), sizeof(int32_t) * m->pperm.size());
     if (tet_perm) std::memcpy(tet_perm, m->tperm.data(), sizeof(int32_t) * m->tperm.size());
+    return TM_OK;
+}
+
+tm_status tm_mesh_export_tet20(const tm_mesh *m, int32_t *vxn, int32_t *n3, int32_t *aos) {
+    if (!m || m->t20.empty()) return TM_ERR_ARG;
+    if (vxn) std::memcpy(vxn, m->t20.data(), sizeof(int32_t) * m->t20.size());
+    if (n3) std::memcpy(n3, m->t20n3.data(), sizeof(int32_t) * m->t20n3.size());
+    if (aos) std::memcpy(aos, m->t20aos.data(), sizeof(int32_t) * m->t20aos.size());
     return TM_OK;
 }
 
@@ -150,6 +161,22 @@ tm_status tm_trace(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_
     if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     const TraceConfig cfg = resolve_trace_opts(opts, m->nt);
+    if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
+    if (cfg.format == TM_FORMAT_TET20_AOS && !m->d_t20aos) return TM_ERR_ARG;
+    return launch_trace(mesh_view(m), rays, n, n_dev, hits, cfg, (cudaStream_t)stream);
+}
+
+tm_status tm_trace_shadow(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_t *n_dev,
+                          int32_t light_tet, tm_hit *hits, const tm_trace_opts *opts, void *stream) {
+    if (!m || n < 0 || (n > 0 && (!rays || !hits))) return TM_ERR_ARG;
+    if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if (light_tet < 0 || light_tet >= m->nt) return TM_ERR_ARG;
+    if (!m->on_device) return TM_ERR_NO_DEVICE;
+    TraceConfig cfg = resolve_trace_opts(opts, m->nt);
+    if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
+    if (cfg.format == TM_FORMAT_TET20_AOS && !m->d_t20aos) return TM_ERR_ARG;
+    cfg.bounded = true;
+    cfg.stop_tet = light_tet;
     return launch_trace(mesh_view(m), rays, n, n_dev, hits, cfg, (cudaStream_t)stream);
 }
 
@@ -170,6 +197,31 @@ tm_status tm_gen_secondary(const tm_mesh *m, const tm_hit *hits, int64_t n, cons
     if (n * (int64_t)per_hit > INT32_MAX) return TM_ERR_TOO_LARGE;
     return launch_gen_secondary(mesh_view(m), hits, n, n_dev, per_hit, tmax, seed, rays_out, count_dev,
                                 src_out, (cudaStream_t)stream);
+}
+
+tm_status tm_gen_shadow(const tm_mesh *m, const tm_hit *hits, int64_t n, const int64_t *n_dev,
+                        float lx, float ly, float lz, tm_ray *rays_out, int64_t *count_dev,
+                        int32_t *src_out, void *stream) {
+    if (!m || n < 0 || !count_dev || (n > 0 && (!hits || !rays_out))) return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if (!(std::isfinite(lx) && std::isfinite(ly) && std::isfinite(lz))) return TM_ERR_ARG;
+    if (!m->on_device) return TM_ERR_NO_DEVICE;
+    if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
+    return launch_gen_shadow(mesh_view(m), hits, n, n_dev, lx, ly, lz, rays_out, count_dev, src_out,
+                             (cudaStream_t)stream);
+}
+
+tm_status tm_gen_specular(const tm_mesh *m, const tm_ray *rays_in, const tm_hit *hits, int64_t n,
+                          const int64_t *n_dev, int kind, float ior, float tmax, tm_ray *rays_out,
+                          int64_t *count_dev, int32_t *src_out, void *stream) {
+    if (!m || n < 0 || !count_dev || (n > 0 && (!hits || !rays_out || !rays_in))) return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits) | ((uintptr_t)rays_in)) & 15u) return TM_ERR_ARG;
+    if (kind != TM_SPECULAR_REFLECT && kind != TM_SPECULAR_REFRACT) return TM_ERR_ARG;
+    if (!(ior > 0.f) || !std::isfinite(ior)) return TM_ERR_ARG;
+    if (!m->on_device) return TM_ERR_NO_DEVICE;
+    if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
+    return launch_gen_specular(mesh_view(m), rays_in, hits, n, n_dev, kind, ior, tmax, rays_out,
+                               count_dev, src_out, (cudaStream_t)stream);
 }
 
 tm_status tm_gen_secondary_noalloc(const tm_mesh *m, const tm_hit *hits, int64_t n,

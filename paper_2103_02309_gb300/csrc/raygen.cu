@@ -1,8 +1,10 @@
 // Ray generation on the device: primary pinhole rays in warp tiles, and
-// secondary rays (diffuse bounce / ambient occlusion) restarted from hit
-// faces into the arrival-side tet (Sec. 6 of the paper), compacted in hit
-// order with a three-pass scan (count per block, scan of the block counts,
-// emit), so the output order does not depend on scheduling.
+// rays restarted from hit faces (Sec. 6 of the paper): diffuse bounce /
+// ambient occlusion and reflection into the arrival-side tet, refraction
+// into the tet across the face, shadow rays into the side facing a point
+// light.  Rays from hits are compacted in hit order with a three-pass scan
+// (count per block, scan of the block counts, emit), so the output order
+// does not depend on scheduling.
 #include <mutex>
 #include <string>
 
@@ -106,20 +108,28 @@ scan_counts_kernel(const int32_t *__restrict__ counts, int64_t nb, int64_t *__re
     }
 }
 
-__global__ void __launch_bounds__(kScanBlock)
-emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
-                      int64_t n, const int64_t *n_dev, const int64_t *__restrict__ offsets,
-                      int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
-                      int32_t *__restrict__ src) {
-    __shared__ int warp_counts[kScanBlock / 32];
-    const int64_t nv = valid_count(n, n_dev);
-    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    int4 h0 = make_int4(-1, 0, 0, 0), h1 = make_int4(0, 0, 0, 0);
+// One hit of the launch, read by the emit kernels.
+struct HitIn {
+    int4 h0, h1;
+    bool hit;
+};
+__device__ __forceinline__ HitIn load_hit(const tm_hit *hits, int64_t i, int64_t nv) {
+    HitIn r;
+    r.h0 = make_int4(-1, 0, 0, 0);
+    r.h1 = make_int4(0, 0, 0, 0);
     if (i < nv) {
-        h0 = __ldcs(reinterpret_cast<const int4 *>(hits + i));
-        h1 = __ldcs(reinterpret_cast<const int4 *>(hits + i) + 1);
+        r.h0 = __ldcs(reinterpret_cast<const int4 *>(hits + i));
+        r.h1 = __ldcs(reinterpret_cast<const int4 *>(hits + i) + 1);
     }
-    const bool hit = h0.x >= 0;
+    r.hit = r.h0.x >= 0;
+    return r;
+}
+
+// Output position of this thread's hit: the block's offset from the scan
+// plus the hits of the lower threads of the block.  Every thread of the
+// block calls it.
+__device__ __forceinline__ int64_t hit_position(bool hit, const int64_t *offsets) {
+    __shared__ int warp_counts[kScanBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned bal = __ballot_sync(0xffffffffu, hit);
     if (lane == 0) warp_counts[warp] = __popc(bal);
@@ -127,18 +137,55 @@ emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restr
     int before = 0;
     for (int w = 0; w < warp; ++w) before += warp_counts[w];
     before += __popc(bal & ((1u << lane) - 1u));
-    if (!hit) return;
-    const int64_t pos = offsets[blockIdx.x] + before;
-    const int32_t c = h1.y;
-    const int side = (h1.w & TM_HIT_SIDE_NEG) ? 1 : 0;
+    return offsets[blockIdx.x] + before;
+}
+
+// The hit point x = a + b1 (b - a) + b2 (c - a) on triangle (a, b, c) (input
+// vertex order) and the unnormalised normal (b - a) x (c - a).
+struct HitGeom {
+    float ox, oy, oz;
+    float nx, ny, nz;
+    float4 a;
+};
+__device__ __forceinline__ HitGeom hit_geometry(const MeshView &mv, const HitIn &h) {
+    HitGeom g;
+    const int32_t c = h.h1.y;
     const int4 cr = __ldg(mv.cface + 2 * c + 1);
     const float4 a = __ldg(mv.pts + cr.x), b = __ldg(mv.pts + cr.y), d = __ldg(mv.pts + cr.z);
-    const float b1 = __int_as_float(h0.z), b2 = __int_as_float(h0.w);
+    const float b1 = __int_as_float(h.h0.z), b2 = __int_as_float(h.h0.w);
     const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
     const float e2x = d.x - a.x, e2y = d.y - a.y, e2z = d.z - a.z;
-    const float ox = a.x + b1 * e1x + b2 * e2x, oy = a.y + b1 * e1y + b2 * e2y,
-                oz = a.z + b1 * e1z + b2 * e2z;
-    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    g.ox = a.x + b1 * e1x + b2 * e2x;
+    g.oy = a.y + b1 * e1y + b2 * e2y;
+    g.oz = a.z + b1 * e1z + b2 * e2z;
+    g.nx = e1y * e2z - e1z * e2y;
+    g.ny = e1z * e2x - e1x * e2z;
+    g.nz = e1x * e2y - e1y * e2x;
+    g.a = a;
+    return g;
+}
+
+__device__ __forceinline__ void put_ray(tm_ray *out, int64_t o, float ox, float oy, float oz,
+                                        int32_t start, float dx, float dy, float dz, float tmax) {
+    float4 *r = reinterpret_cast<float4 *>(out + o);
+    __stcs(r, make_float4(ox, oy, oz, __int_as_float(start)));
+    __stcs(r + 1, make_float4(dx, dy, dz, tmax));
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
+                      int64_t n, const int64_t *n_dev, const int64_t *__restrict__ offsets,
+                      int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
+                      int32_t *__restrict__ src) {
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    const HitIn h = load_hit(hits, i, valid_count(n, n_dev));
+    const int64_t pos = hit_position(h.hit, offsets);
+    if (!h.hit) return;
+    const int32_t c = h.h1.y;
+    const int side = (h.h1.w & TM_HIT_SIDE_NEG) ? 1 : 0;
+    const HitGeom g = hit_geometry(mv, h);
+    const float ox = g.ox, oy = g.oy, oz = g.oz;
+    float nx = g.nx, ny = g.ny, nz = g.nz;
     const float inv = rsqrtf(nx * nx + ny * ny + nz * nz) * (side ? -1.f : 1.f);
     nx *= inv; ny *= inv; nz *= inv;
     // orthonormal basis around n (Duff et al., JCGT 2017)
@@ -159,11 +206,75 @@ emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restr
         const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= il; dy *= il; dz *= il;
         const int64_t o = pos * per_hit + k;
-        float4 *r = reinterpret_cast<float4 *>(out + o);
-        __stcs(r, make_float4(ox, oy, oz, __int_as_float(start)));
-        __stcs(r + 1, make_float4(dx, dy, dz, tmax));
+        put_ray(out, o, ox, oy, oz, start, dx, dy, dz, tmax);
         if (src) src[o] = (int32_t)i;
     }
+}
+
+// Shadow rays: from the hit point toward the point light, restarted into
+// the side of the hit triangle that faces the light, tmax = the distance.
+__global__ void __launch_bounds__(kScanBlock)
+emit_shadow_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits, int64_t n,
+                   const int64_t *n_dev, const int64_t *__restrict__ offsets, float lx, float ly,
+                   float lz, tm_ray *__restrict__ out, int32_t *__restrict__ src) {
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    const HitIn h = load_hit(hits, i, valid_count(n, n_dev));
+    const int64_t pos = hit_position(h.hit, offsets);
+    if (!h.hit) return;
+    const int32_t c = h.h1.y;
+    const HitGeom g = hit_geometry(mv, h);
+    const float facing = g.nx * (lx - g.a.x) + g.ny * (ly - g.a.y) + g.nz * (lz - g.a.z);
+    const int side = facing >= 0.f ? 0 : 1;
+    float vx = lx - g.ox, vy = ly - g.oy, vz = lz - g.oz;
+    const float len = sqrtf(vx * vx + vy * vy + vz * vz);
+    if (len > 0.f) {
+        const float il = 1.f / len;
+        vx *= il; vy *= il; vz *= il;
+    } else {  // the light sits on the hit point: an empty segment along the normal
+        const float il = (side ? -1.f : 1.f) / sqrtf(g.nx * g.nx + g.ny * g.ny + g.nz * g.nz);
+        vx = g.nx * il; vy = g.ny * il; vz = g.nz * il;
+    }
+    put_ray(out, pos, g.ox, g.oy, g.oz, -1 - (2 * c + side), vx, vy, vz, len);
+    if (src) src[pos] = (int32_t)i;
+}
+
+// Reflection / refraction rays (directions in the header's notation).
+__global__ void __launch_bounds__(kScanBlock)
+emit_specular_kernel(const __grid_constant__ MeshView mv, const tm_ray *__restrict__ rays_in,
+                     const tm_hit *__restrict__ hits, int64_t n, const int64_t *n_dev,
+                     const int64_t *__restrict__ offsets, int kind, float ior, float tmax,
+                     tm_ray *__restrict__ out, int32_t *__restrict__ src) {
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    const HitIn h = load_hit(hits, i, valid_count(n, n_dev));
+    const int64_t pos = hit_position(h.hit, offsets);
+    if (!h.hit) return;
+    const int32_t c = h.h1.y;
+    const int side = (h.h1.w & TM_HIT_SIDE_NEG) ? 1 : 0;  // arrival side
+    const HitGeom g = hit_geometry(mv, h);
+    const float4 din = __ldg(reinterpret_cast<const float4 *>(rays_in + i) + 1);
+    const float iw = 1.f / sqrtf(din.x * din.x + din.y * din.y + din.z * din.z);
+    const float wx = din.x * iw, wy = din.y * iw, wz = din.z * iw;
+    const float in = (side ? -1.f : 1.f) / sqrtf(g.nx * g.nx + g.ny * g.ny + g.nz * g.nz);
+    const float nx = g.nx * in, ny = g.ny * in, nz = g.nz * in;  // toward the arrival side
+    const float cs = fmaxf(0.f, -(wx * nx + wy * ny + wz * nz));
+    float dx, dy, dz;
+    int out_side = side;
+    const float eta = side ? ior : 1.f / ior;
+    const float k = 1.f - eta * eta * (1.f - cs * cs);
+    if (kind == TM_SPECULAR_REFRACT && k >= 0.f) {
+        const float f = eta * cs - sqrtf(k);
+        dx = eta * wx + f * nx;
+        dy = eta * wy + f * ny;
+        dz = eta * wz + f * nz;
+        out_side = 1 - side;
+    } else {
+        dx = wx + 2.f * cs * nx;
+        dy = wy + 2.f * cs * ny;
+        dz = wz + 2.f * cs * nz;
+    }
+    const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+    put_ray(out, pos, g.ox, g.oy, g.oz, -1 - (2 * c + out_side), dx * il, dy * il, dz * il, tmax);
+    if (src) src[pos] = (int32_t)i;
 }
 
 }  // namespace tmk
@@ -184,9 +295,13 @@ tm_status launch_gen_primary(const tm_camera *cam, const int32_t *start, float t
     return TM_OK;
 }
 
-tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n,
-                               const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
-                               tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
+namespace {
+
+// Count, scan and emit with cudaMallocAsync scratch; `emit(nb, offsets)`
+// launches the emit kernel.
+template <class Emit>
+tm_status gen_from_hits(const tm_hit *hits, int64_t n, const int64_t *n_dev, int per_hit,
+                        int64_t *count, cudaStream_t s, const char *what, Emit emit) {
     using tmk::kScanBlock;
     if (n == 0) {
         TM_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
@@ -200,17 +315,48 @@ tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n
     TM_CUDA(cudaMallocAsync((void **)&offsets, sizeof(int64_t) * (nb + 1), s));
     tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, counts);
     tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb, offsets, per_hit, count);
-    tmk::emit_secondary_kernel<<<(int)nb, kScanBlock, 0, s>>>(mv, hits, n, n_dev, offsets, per_hit,
-                                                             tmax, seed, out, src);
+    emit((int)nb, offsets);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(counts, s);
     cudaFreeAsync(offsets, s);
     if (e != cudaSuccess) {
-        tm_set_error("gen_secondary launch", e);
+        tm_set_error(what, e);
         return TM_ERR_CUDA;
     }
     tm_count_launches(3);
     return TM_OK;
+}
+
+}  // namespace
+
+tm_status launch_gen_shadow(const MeshView &mv, const tm_hit *hits, int64_t n, const int64_t *n_dev,
+                            float lx, float ly, float lz, tm_ray *out, int64_t *count, int32_t *src,
+                            cudaStream_t s) {
+    return gen_from_hits(hits, n, n_dev, 1, count, s, "gen_shadow launch",
+                         [&](int nb, const int64_t *offsets) {
+                             tmk::emit_shadow_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
+                                 mv, hits, n, n_dev, offsets, lx, ly, lz, out, src);
+                         });
+}
+
+tm_status launch_gen_specular(const MeshView &mv, const tm_ray *rays_in, const tm_hit *hits,
+                              int64_t n, const int64_t *n_dev, int kind, float ior, float tmax,
+                              tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
+    return gen_from_hits(hits, n, n_dev, 1, count, s, "gen_specular launch",
+                         [&](int nb, const int64_t *offsets) {
+                             tmk::emit_specular_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
+                                 mv, rays_in, hits, n, n_dev, offsets, kind, ior, tmax, out, src);
+                         });
+}
+
+tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n,
+                               const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
+                               tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
+    return gen_from_hits(hits, n, n_dev, per_hit, count, s, "gen_secondary launch",
+                         [&](int nb, const int64_t *offsets) {
+                             tmk::emit_secondary_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
+                                 mv, hits, n, n_dev, offsets, per_hit, tmax, seed, out, src);
+                         });
 }
 
 // ---------------------------------------------------------------------------

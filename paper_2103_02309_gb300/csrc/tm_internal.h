@@ -26,6 +26,9 @@ struct tm_mesh {
     std::vector<int32_t> cold;   // nt*8: V0..V3 (positive orientation), N0..N3 (N_j across V_j)
     std::vector<float> pts4;     // np*4
     std::vector<int32_t> cface;  // nc*8: tri, tet+, tet-, 0, v0, v1, v2, 0
+    std::vector<int32_t> t20;    // nt*4: VX, N0, N1, N2 (neighbours by rank), when built
+    std::vector<int32_t> t20n3;  // nt: N3, when built
+    std::vector<int32_t> t20aos; // nt*5: VX, N0..N3 at a 20-byte stride, when built
     std::vector<int32_t> pperm, tperm;  // internal -> input
     std::vector<int32_t> pinv, tinv;    // input -> internal
     // device copies
@@ -36,6 +39,9 @@ struct tm_mesh {
     int4 *d_cold = nullptr;
     int4 *d_cface = nullptr;
     int32_t *d_seeds = nullptr;  // located tets of a kSeedGrid^3 lattice over the bounding box
+    int4 *d_t20 = nullptr;
+    int32_t *d_t20n3 = nullptr;
+    int32_t *d_t20aos = nullptr;
     int64_t device_bytes = 0;
 };
 
@@ -52,6 +58,9 @@ struct MeshView {
     int32_t nt, np, nc;
     float extent;
     const int32_t *seeds;  // kSeedGrid^3 source tets for point location (may be null)
+    const int4 *t20;       // Tet20 {VX, N0, N1, N2} (may be null)
+    const int32_t *t20n3;  // Tet20 N3 (may be null)
+    const int32_t *t20aos; // Tet20 packed {VX, N0..N3} (may be null)
     float lo[3], cell_inv;  // lattice origin and kSeedGrid / extent
 };
 
@@ -66,6 +75,9 @@ inline MeshView mesh_view(const tm_mesh *m) {
     v.nc = (int32_t)m->nc;
     v.extent = (float)m->extent;
     v.seeds = m->d_seeds;
+    v.t20 = m->d_t20;
+    v.t20n3 = m->d_t20n3;
+    v.t20aos = m->d_t20aos;
     for (int a = 0; a < 3; ++a) v.lo[a] = m->lo[a];
     v.cell_inv = m->extent > 0 ? (float)(kSeedGrid / m->extent) : 0.f;
     return v;
@@ -96,6 +108,8 @@ struct TraceConfig {
     int ctas_per_sm;
     bool bounded;
     cudaEvent_t events[4];
+    int format;
+    int32_t stop_tet;  // point-light rays: stop on entering this tet (-1: none); needs bounded
 };
 TraceConfig resolve_trace_opts(const tm_trace_opts *opts, int64_t nt);
 
@@ -108,6 +122,13 @@ tm_status launch_gen_primary(const tm_camera *cam, const int32_t *start, float t
 tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n,
                                const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                                tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s);
+
+tm_status launch_gen_shadow(const MeshView &mv, const tm_hit *hits, int64_t n, const int64_t *n_dev,
+                            float lx, float ly, float lz, tm_ray *out, int64_t *count, int32_t *src,
+                            cudaStream_t s);
+tm_status launch_gen_specular(const MeshView &mv, const tm_ray *rays_in, const tm_hit *hits,
+                              int64_t n, const int64_t *n_dev, int kind, float ior, float tmax,
+                              tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s);
 
 tm_status launch_gen_secondary_noalloc(const MeshView &mv, const tm_hit *hits, int64_t n,
                                        const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,

@@ -72,7 +72,8 @@ __device__ __forceinline__ Slot find_slot(const BatchDesc *d, int n_meshes, unsi
 struct PhaseParams {
     int64_t n_cap;
     const int64_t *n_dev;
-    float tau_rel;  // sign-test guard threshold relative to the mesh extent
+    float tau_rel;    // sign-test guard threshold relative to the mesh extent
+    int32_t stop_tet; // point-light rays: the tet that holds the light, else -1
 };
 
 __device__ __forceinline__ int64_t ray_count(const PhaseParams &P) {
@@ -133,7 +134,7 @@ __device__ __noinline__ int32_t search_start(const MeshView mv, const tm_ray *rp
 // Phase 1 for one ray.
 template <int MODE>
 __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
-                                          float tau_rel) {
+                                          float tau_rel, int32_t stop_tet) {
     typedef typename RealOf<MODE>::T R;
     const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(rp));
     const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(rp) + 1);
@@ -196,8 +197,12 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
     }
     if (!ok)
         put_end(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_START);
+    else if (T == stop_tet)  // the ray starts in the light's tet: nothing lies in between
+        put_end(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
     else if (next & TM_CFACE_FLAG)
         put_end(hp, S.prev, next, steps, sc.flags);
+    else if ((int32_t)next == stop_tet)
+        put_end(hp, (int32_t)next, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
     else
         put_record(hp, 0, (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
 }
@@ -213,9 +218,9 @@ start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
         if (MULTI) {
             const Slot s = find_slot(descs, n_meshes, (unsigned long long)r);
             const BatchDesc &D = descs[s.m];
-            start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel);
+            start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel, -1);
         } else {
-            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel);
+            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, P.stop_tet);
         }
     }
 }
@@ -321,6 +326,73 @@ template <class R> struct Depth<R, true> {
     __device__ __forceinline__ bool beyond() const { return fmin(z0, fmin(z1, z2)) > zmax; }
 };
 
+// One tet record in the walk's format, and the decode of the neighbour across
+// the exit vertex ie (Sec. 3 and Alg. 3, 5, 7).  i0..i2 are the entry face,
+// i3 the new vertex; prev is the tet the walk came from.
+template <int FMT> struct TetRec;
+
+template <> struct TetRec<TM_FORMAT_TET16> {  // VX, NX_j = N_j ^ N_3, neighbours by vertex rank
+    int4 r;
+    __device__ __forceinline__ void load(const MeshView &, const int4 *tet16, int32_t t) {
+        r = __ldg(tet16 + t);
+    }
+    __device__ __forceinline__ int32_t vx() const { return r.x; }
+    __device__ __forceinline__ uint32_t next(int32_t prev, int32_t i0, int32_t i1, int32_t i2,
+                                             int32_t i3, int32_t ie) const {
+        const int ra = (i0 < i3) + (i1 < i3) + (i2 < i3);
+        const int rb = (i0 < ie) + (i1 < ie) + (i2 < ie) + (i3 < ie);
+        const uint32_t nxa = ra == 0 ? r.y : (ra == 1 ? r.z : (ra == 2 ? r.w : 0));
+        const uint32_t nxb = rb == 0 ? r.y : (rb == 1 ? r.z : (rb == 2 ? r.w : 0));
+        return (uint32_t)prev ^ nxa ^ nxb;
+    }
+};
+
+template <> struct TetRec<TM_FORMAT_TET20> {  // VX, N_0..N_3 by vertex rank
+    int4 r;
+    int32_t n3;
+    __device__ __forceinline__ void load(const MeshView &mv, const int4 *, int32_t t) {
+        r = __ldg(mv.t20 + t);
+        n3 = __ldg(mv.t20n3 + t);
+    }
+    __device__ __forceinline__ int32_t vx() const { return r.x; }
+    __device__ __forceinline__ uint32_t next(int32_t, int32_t i0, int32_t i1, int32_t i2, int32_t i3,
+                                             int32_t ie) const {
+        const int rb = (i0 < ie) + (i1 < ie) + (i2 < ie) + (i3 < ie);
+        return (uint32_t)(rb == 0 ? r.y : (rb == 1 ? r.z : (rb == 2 ? r.w : n3)));
+    }
+};
+
+template <> struct TetRec<TM_FORMAT_TET20_AOS> {  // the same, packed at a 20-byte stride
+    int32_t vx_, n[4];
+    __device__ __forceinline__ void load(const MeshView &mv, const int4 *, int32_t t) {
+        const int32_t *p = mv.t20aos + 5 * (int64_t)t;
+        vx_ = __ldg(p);
+        n[0] = __ldg(p + 1);
+        n[1] = __ldg(p + 2);
+        n[2] = __ldg(p + 3);
+        n[3] = __ldg(p + 4);
+    }
+    __device__ __forceinline__ int32_t vx() const { return vx_; }
+    __device__ __forceinline__ uint32_t next(int32_t, int32_t i0, int32_t i1, int32_t i2, int32_t i3,
+                                             int32_t ie) const {
+        const int rb = (i0 < ie) + (i1 < ie) + (i2 < ie) + (i3 < ie);
+        return (uint32_t)(rb == 0 ? n[0] : (rb == 1 ? n[1] : (rb == 2 ? n[2] : n[3])));
+    }
+};
+
+template <> struct TetRec<TM_FORMAT_TET32> {  // V_0..V_3 and N_j across V_j (the cold record)
+    int4 v, nb;
+    __device__ __forceinline__ void load(const MeshView &mv, const int4 *, int32_t t) {
+        v = __ldg(mv.cold + 2 * t);
+        nb = __ldg(mv.cold + 2 * t + 1);
+    }
+    __device__ __forceinline__ int32_t vx() const { return v.x ^ v.y ^ v.z ^ v.w; }
+    __device__ __forceinline__ uint32_t next(int32_t, int32_t, int32_t, int32_t, int32_t,
+                                             int32_t ie) const {
+        return (uint32_t)(ie == v.x ? nb.x : (ie == v.y ? nb.y : (ie == v.z ? nb.z : nb.w)));
+    }
+};
+
 struct WalkParams {
     int64_t n_cap;
     const int64_t *n_dev;
@@ -329,6 +401,7 @@ struct WalkParams {
     float tau_rel;
     int refill;
     int batch_steps;
+    int32_t stop_tet;  // point-light rays (bounded walks only): the light's tet, else -1
 };
 
 // Guard mode: one step of a parked ray, with the double-precision re-test of
@@ -336,9 +409,9 @@ struct WalkParams {
 // undecided).  Reads the walk record from the hit slot and writes back the
 // record of the next tet, or the end record.  Out of line: no walk state is
 // live across the call, so the walk loop keeps its small register budget.
-template <bool BOUNDED>
+template <int FMT, bool BOUNDED>
 __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp, tm_hit *hp,
-                                            float tau_rel, uint32_t max_steps) {
+                                            float tau_rel, uint32_t max_steps, int32_t stop_tet) {
     typedef float R;
     const int4 a = __ldcg(reinterpret_cast<const int4 *>(hp));
     const int4 b = __ldcg(reinterpret_cast<const int4 *>(hp) + 1);
@@ -364,8 +437,9 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
     S.m0 = guard_mag(S.p0, sc.tau);
     S.m1 = guard_mag(S.p1, sc.tau);
     S.m2 = guard_mag(S.p2, sc.tau);
-    const int4 rec = __ldg(mv.tet16 + S.tet);
-    const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.x;
+    TetRec<FMT> rec;
+    rec.load(mv, mv.tet16, S.tet);
+    const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.vx();
     if ((uint32_t)i3 >= (uint32_t)mv.np) {
         put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
         return;
@@ -374,12 +448,8 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
     const P2<R> p3 = B.project(x.x, x.y, x.z);
     const float m3 = guard_mag(p3, sc.tau);
     const int e = exit_slot_bits(step_signs<FP32G, false, true>(S, p3, i3, m3, sc));
-    const int ra = (S.i0 < i3) + (S.i1 < i3) + (S.i2 < i3);
     const int32_t ie = e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2);
-    const int rb = (S.i0 < ie) + (S.i1 < ie) + (S.i2 < ie) + (i3 < ie);
-    const uint32_t nxa = ra == 0 ? rec.y : (ra == 1 ? rec.z : (ra == 2 ? rec.w : 0));
-    const uint32_t nxb = rb == 0 ? rec.y : (rb == 1 ? rec.z : (rb == 2 ? rec.w : 0));
-    const uint32_t next = (uint32_t)S.prev ^ nxa ^ nxb;
+    const uint32_t next = rec.next(S.prev, S.i0, S.i1, S.i2, i3, ie);
     float4 xf[3] = {x0, x1, x2};
     if (e == 0) S.i0 = i3; else if (e == 1) S.i1 = i3; else S.i2 = i3;
     xf[e] = x;
@@ -390,6 +460,8 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
         put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
     } else if (steps >= max_steps) {
         put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_STEP_LIMIT);
+    } else if (BOUNDED && next == (uint32_t)stop_tet) {
+        put_end(hp, (int32_t)next, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
     } else {
         if (BOUNDED) {
             Depth<R, true> Z;
@@ -415,7 +487,7 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
 #define TM_WALK_MAXREG_FP64 72
 #endif
 
-template <int MODE, bool BOUNDED, bool MULTI>
+template <int MODE, int FMT, bool BOUNDED, bool MULTI>
 __global__ void __maxnreg__(MODE == FP64 ? TM_WALK_MAXREG_FP64 : TM_WALK_MAXREG)
 walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
             tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
@@ -449,7 +521,8 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
         bool load = false;
         if (MODE == FP32G && parked) {
             // re-decide the step this lane parked, then go on from its new record
-            resolve_parked<BOUNDED>(MULTI ? sdesc[m].mesh : mv0, sc.ray, hp, P.tau_rel, P.max_steps);
+            resolve_parked<FMT, BOUNDED>(MULTI ? sdesc[m].mesh : mv0, sc.ray, hp, P.tau_rel,
+                                         P.max_steps, P.stop_tet);
             parked = false;
             load = true;
         }
@@ -523,9 +596,10 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
         }
         for (int k = 0; k < P.batch_steps; ++k) {
             if (!active) continue;
-            // ---- one step of Alg. 6 / Alg. 7 ----
-            const int4 rec = __ldg(tet16 + S.tet);
-            const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.x;
+            // ---- one step of Alg. 6 / Alg. 7 (or Alg. 4-5, Alg. 2-3) ----
+            TetRec<FMT> rec;
+            rec.load(mv0, tet16, S.tet);
+            const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.vx();
             uint32_t code = TM_BOUNDARY;
             bool done = false;
             if ((uint32_t)i3 >= (uint32_t)(MULTI ? sdesc[m].mesh.np : mv0.np)) {
@@ -546,12 +620,8 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     continue;
                 }
                 const int e = exit_slot_bits(sig);
-                const int ra = (S.i0 < i3) + (S.i1 < i3) + (S.i2 < i3);
                 const int32_t ie = e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2);
-                const int rb = (S.i0 < ie) + (S.i1 < ie) + (S.i2 < ie) + (i3 < ie);
-                const uint32_t nxa = ra == 0 ? rec.y : (ra == 1 ? rec.z : (ra == 2 ? rec.w : 0));
-                const uint32_t nxb = rb == 0 ? rec.y : (rb == 1 ? rec.z : (rb == 2 ? rec.w : 0));
-                const uint32_t next = (uint32_t)S.prev ^ nxa ^ nxb;
+                const uint32_t next = rec.next(S.prev, S.i0, S.i1, S.i2, i3, ie);
                 if (e == 0) { S.i0 = i3; S.p0 = p3; S.m0 = m3; }
                 else if (e == 1) { S.i1 = i3; S.p1 = p3; S.m1 = m3; }
                 else { S.i2 = i3; S.p2 = p3; S.m2 = m3; }
@@ -568,6 +638,12 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     done = true;
                     code = TM_BOUNDARY;
                     sc.flags |= TM_HIT_STEP_LIMIT;
+                } else if (BOUNDED && next == (uint32_t)P.stop_tet) {
+                    // reached the tet that holds the point light (Sec. 6)
+                    done = true;
+                    code = TM_BOUNDARY;
+                    sc.flags |= TM_HIT_REACHED;
+                    S.tet = (int32_t)next;
                 } else if (BOUNDED && Z.beyond()) {
                     done = true;
                     code = TM_BOUNDARY;
@@ -601,24 +677,25 @@ int sm_count_cached() {
     return count;
 }
 
-template <int MODE, bool BOUNDED, bool MULTI>
+template <int MODE, int FMT, bool BOUNDED, bool MULTI>
 int walk_occupancy(int block, size_t smem) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<MODE, BOUNDED, MULTI>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel<MODE, FMT, BOUNDED, MULTI>, block,
+                                                  smem);
     return nb;
 }
 
 template <bool BOUNDED, bool MULTI>
 int occupancy_mode(int mode, int block, size_t smem) {
     switch (mode) {
-        case FP32G: return walk_occupancy<FP32G, BOUNDED, MULTI>(block, smem);
-        case FP32: return walk_occupancy<FP32, BOUNDED, MULTI>(block, smem);
-        default: return walk_occupancy<FP64, BOUNDED, MULTI>(block, smem);
+        case FP32G: return walk_occupancy<FP32G, TM_FORMAT_TET16, BOUNDED, MULTI>(block, smem);
+        case FP32: return walk_occupancy<FP32, TM_FORMAT_TET16, BOUNDED, MULTI>(block, smem);
+        default: return walk_occupancy<FP64, TM_FORMAT_TET16, BOUNDED, MULTI>(block, smem);
     }
 }
 
 // Launches start, walk and finish for one mode.
-template <int MODE, bool BOUNDED, bool MULTI>
+template <int MODE, int FMT, bool BOUNDED, bool MULTI>
 cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, const BatchDesc *descs,
                           int n_meshes, const WalkParams &W, int block, int walk_grid,
                           const cudaEvent_t *ev, cudaStream_t s) {
@@ -626,6 +703,7 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     P.n_cap = W.n_cap;
     P.n_dev = W.n_dev;
     P.tau_rel = W.tau_rel;
+    P.stop_tet = MULTI ? -1 : W.stop_tet;
     const int sms = sm_count_cached();
     int64_t g = (W.n_cap + 255) / 256;
     const int64_t gmax = (int64_t)sms * 16;
@@ -634,21 +712,38 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     start_kernel<MODE, MULTI><<<(int)g, 256, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
     if (ev && ev[1]) cudaEventRecord(ev[1], s);
     const size_t smem = MULTI ? sizeof(BatchDesc) * (size_t)n_meshes : 0;
-    walk_kernel<MODE, BOUNDED, MULTI><<<walk_grid, block, smem, s>>>(mv, rays, hits, descs, n_meshes, W);
+    walk_kernel<MODE, FMT, BOUNDED, MULTI><<<walk_grid, block, smem, s>>>(mv, rays, hits, descs,
+                                                                           n_meshes, W);
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
     finish_kernel<MODE, MULTI><<<(int)g, 256, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
+template <int FMT, bool BOUNDED, bool MULTI>
+cudaError_t dispatch_fmt(int mode, const MeshView &mv, const tm_ray *rays, tm_hit *hits,
+                         const BatchDesc *descs, int n_meshes, const WalkParams &W, int block,
+                         int grid, const cudaEvent_t *ev, cudaStream_t s) {
+    switch (mode) {
+        case FP32G: return launch_phases<FP32G, FMT, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+        case FP32: return launch_phases<FP32, FMT, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+        default: return launch_phases<FP64, FMT, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+    }
+}
+
 template <bool BOUNDED, bool MULTI>
-cudaError_t dispatch(int mode, const MeshView &mv, const tm_ray *rays, tm_hit *hits,
+cudaError_t dispatch(int mode, int format, const MeshView &mv, const tm_ray *rays, tm_hit *hits,
                      const BatchDesc *descs, int n_meshes, const WalkParams &W, int block, int grid,
                      const cudaEvent_t *ev, cudaStream_t s) {
-    switch (mode) {
-        case FP32G: return launch_phases<FP32G, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
-        case FP32: return launch_phases<FP32, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
-        default: return launch_phases<FP64, BOUNDED, MULTI>(mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+    if constexpr (MULTI) {  // batches walk the Tet16 records
+        return dispatch_fmt<TM_FORMAT_TET16, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+    } else {
+        switch (format) {
+            case TM_FORMAT_TET20: return dispatch_fmt<TM_FORMAT_TET20, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            case TM_FORMAT_TET32: return dispatch_fmt<TM_FORMAT_TET32, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            case TM_FORMAT_TET20_AOS: return dispatch_fmt<TM_FORMAT_TET20_AOS, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            default: return dispatch_fmt<TM_FORMAT_TET16, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+        }
     }
 }
 
@@ -677,11 +772,16 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
     for (int i = 0; i < 4; ++i) c.events[i] = o ? (cudaEvent_t)o->phase_events[i] : nullptr;
+    c.format = o ? o->format : TM_FORMAT_TET16;
+    c.stop_tet = -1;
     return c;
 }
 
 static bool valid_config(const TraceConfig &c) {
-    return (c.mode == FP32G || c.mode == FP32 || c.mode == FP64) && c.block >= 32 &&
+    return (c.mode == FP32G || c.mode == FP32 || c.mode == FP64) &&
+           (c.format == TM_FORMAT_TET16 || c.format == TM_FORMAT_TET20 || c.format == TM_FORMAT_TET32 ||
+            c.format == TM_FORMAT_TET20_AOS) &&
+           c.block >= 32 &&
            c.block <= 1024 && c.block % 32 == 0 && c.refill >= 1 && c.refill <= 32 &&
            c.batch_steps >= 1 && c.batch_steps <= 256 && c.ctas_per_sm >= 0;
 }
@@ -702,6 +802,7 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
     W.tau_rel = cfg.tau;
     W.refill = cfg.refill;
     W.batch_steps = cfg.batch_steps;
+    W.stop_tet = cfg.stop_tet;
     int sms = 0;
     int per_sm = max_persistent_ctas(cfg.mode, false, cfg.bounded, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
@@ -709,8 +810,8 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
     const int64_t need = (n + cfg.block - 1) / cfg.block;
     if (!n_dev && grid > need) grid = need;
     cudaError_t e = cfg.bounded
-        ? dispatch<true, false>(cfg.mode, mv, rays, hits, nullptr, 0, W, cfg.block, (int)grid, cfg.events, s)
-        : dispatch<false, false>(cfg.mode, mv, rays, hits, nullptr, 0, W, cfg.block, (int)grid, cfg.events, s);
+        ? dispatch<true, false>(cfg.mode, cfg.format, mv, rays, hits, nullptr, 0, W, cfg.block, (int)grid, cfg.events, s)
+        : dispatch<false, false>(cfg.mode, cfg.format, mv, rays, hits, nullptr, 0, W, cfg.block, (int)grid, cfg.events, s);
     if (e != cudaSuccess) {
         tm_set_error("trace launch", e);
         cudaFreeAsync(cursor, s);
@@ -734,6 +835,7 @@ tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t t
     W.tau_rel = cfg.tau;
     W.refill = cfg.refill;
     W.batch_steps = cfg.batch_steps;
+    W.stop_tet = -1;
     int sms = 0;
     int per_sm = max_persistent_ctas(cfg.mode, true, false, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
@@ -742,8 +844,9 @@ tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t t
     if (grid > need) grid = need;
     TM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
     MeshView dummy{};
-    cudaError_t e = dispatch<false, true>(cfg.mode, dummy, nullptr, nullptr, descs_dev, n_meshes, W,
-                                          cfg.block, (int)grid, nullptr, s);
+    if (cfg.format != TM_FORMAT_TET16) return TM_ERR_ARG;
+    cudaError_t e = dispatch<false, true>(cfg.mode, TM_FORMAT_TET16, dummy, nullptr, nullptr, descs_dev,
+                                          n_meshes, W, cfg.block, (int)grid, nullptr, s);
     if (e != cudaSuccess) {
         tm_set_error("trace (batch) launch", e);
         return TM_ERR_CUDA;

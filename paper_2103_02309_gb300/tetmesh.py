@@ -18,6 +18,7 @@ import torch
 from . import _native as N
 
 MODES = {"fp32g": 0, "fp32": 1, "fp64": 2}
+FORMATS = {"tet16": 0, "tet20": 1, "tet32": 2, "tet20_aos": 3}
 ORDERS = {"hilbert": 0, "input": 1}
 
 HIT_SIDE_NEG = 0x01
@@ -30,6 +31,8 @@ HIT_RESTART_3D = 0x40
 HIT_BAD_ID = 0x80
 HIT_START_MOVED = 0x100
 HIT_SLOW_PASS = 0x200
+HIT_REACHED = 0x400
+SPECULAR = {"reflect": 0, "refract": 1}
 
 IDS_TET, IDS_POINT = 0, 1
 TO_INPUT, TO_INTERNAL = 0, 1
@@ -55,7 +58,7 @@ def _hptr(a: np.ndarray):
 
 
 def trace_opts(mode="fp32g", guard_tau=0.0, max_steps=0, block=0, refill=0, batch_steps=0,
-               ctas_per_sm=0, tmax_early_exit=False, phase_events=None) -> N.TraceOpts:
+               ctas_per_sm=0, tmax_early_exit=False, phase_events=None, format="tet16") -> N.TraceOpts:
     """Trace options; phase_events: four torch.cuda.Event (enable_timing) recorded
     before the start phase, after it, after the walk and after the finish phase."""
     o = N.TraceOpts()
@@ -67,6 +70,7 @@ def trace_opts(mode="fp32g", guard_tau=0.0, max_steps=0, block=0, refill=0, batc
     o.batch_steps = int(batch_steps)
     o.ctas_per_sm = int(ctas_per_sm)
     o.tmax_early_exit = 1 if tmax_early_exit else 0
+    o.format = FORMATS[format] if isinstance(format, str) else int(format)
     if phase_events is not None:
         for i, ev in enumerate(phase_events):
             o.phase_events[i] = ev.cuda_event if ev is not None else None
@@ -117,11 +121,12 @@ def make_camera(eye, fov_deg, width, height) -> N.Camera:
 class Mesh:
     """A compact constrained tet mesh on the current CUDA device."""
 
-    def __init__(self, points, tets, tris, order="hilbert", upload=True, fix_orientation=False):
+    def __init__(self, points, tets, tris, order="hilbert", upload=True, fix_orientation=False,
+                 tet20=False):
         pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
         tt = np.ascontiguousarray(tets, np.int32).reshape(-1, 4)
         tr = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
-        o = N.BuildOpts(ORDERS[order], 1 if fix_orientation else 0)
+        o = N.BuildOpts(ORDERS[order], 1 if fix_orientation else 0, 1 if tet20 else 0)
         h = ctypes.c_void_p()
         N.check(N.lib.tm_build(_hptr(pts), len(pts), _hptr(tt), len(tt),
                                _hptr(tr) if len(tr) else None, len(tr), ctypes.byref(o),
@@ -161,6 +166,14 @@ class Mesh:
         out["cface"] = out["cface"][:nc]
         return out
 
+    def export_tet20(self) -> dict:
+        vxn = np.empty((self.n_tets, 4), np.int32)
+        n3 = np.empty(self.n_tets, np.int32)
+        aos = np.empty((self.n_tets, 5), np.int32)
+        N.check(N.lib.tm_mesh_export_tet20(self._h, _hptr(vxn), _hptr(n3), _hptr(aos)),
+                "tm_mesh_export_tet20")
+        return dict(vxn=vxn, n3=n3, aos=aos)
+
     def map_ids(self, kind, direction, ids) -> np.ndarray:
         a = np.ascontiguousarray(ids, np.int32).reshape(-1)
         out = np.empty_like(a)
@@ -188,6 +201,53 @@ class Mesh:
         N.check(N.lib.tm_trace(self._h, _dptr(rays), n, _dptr(n_dev), _dptr(hits),
                                ctypes.byref(o), _stream(stream)), "tm_trace")
         return hits
+
+    def trace_shadow(self, rays: torch.Tensor, light_tet: int, hits: torch.Tensor | None = None,
+                     n_dev: torch.Tensor | None = None, opts: N.TraceOpts | None = None,
+                     stream=None, **kw) -> torch.Tensor:
+        """Walks that also end (flag HIT_REACHED) on entering the light's tet."""
+        n = rays.shape[0]
+        if hits is None:
+            hits = torch.empty((n, 8), dtype=torch.int32, device=rays.device)
+        o = opts if opts is not None else trace_opts(**kw)
+        N.check(N.lib.tm_trace_shadow(self._h, _dptr(rays), n, _dptr(n_dev), int(light_tet),
+                                      _dptr(hits), ctypes.byref(o), _stream(stream)),
+                "tm_trace_shadow")
+        return hits
+
+    def _outputs(self, n, device, rays_out, count, src):
+        if rays_out is None:
+            rays_out = torch.empty((n, 8), dtype=torch.float32, device=device)
+        if count is None:
+            count = torch.empty(1, dtype=torch.int64, device=device)
+        if src is True:
+            src = torch.empty(n, dtype=torch.int32, device=device)
+        elif src is False:
+            src = None
+        return rays_out, count, src
+
+    def gen_shadow(self, hits: torch.Tensor, light, n_dev: torch.Tensor | None = None,
+                   rays_out: torch.Tensor | None = None, count: torch.Tensor | None = None,
+                   src: bool | torch.Tensor = False, stream=None):
+        n = hits.shape[0]
+        rays_out, count, src = self._outputs(n, hits.device, rays_out, count, src)
+        lx, ly, lz = (float(v) for v in light)
+        N.check(N.lib.tm_gen_shadow(self._h, _dptr(hits), n, _dptr(n_dev), lx, ly, lz,
+                                    _dptr(rays_out), _dptr(count), _dptr(src), _stream(stream)),
+                "tm_gen_shadow")
+        return rays_out, count, src
+
+    def gen_specular(self, rays_in: torch.Tensor, hits: torch.Tensor, kind: str, ior: float,
+                     tmax: float = float("inf"), n_dev: torch.Tensor | None = None,
+                     rays_out: torch.Tensor | None = None, count: torch.Tensor | None = None,
+                     src: bool | torch.Tensor = False, stream=None):
+        n = hits.shape[0]
+        rays_out, count, src = self._outputs(n, hits.device, rays_out, count, src)
+        k = SPECULAR[kind] if isinstance(kind, str) else int(kind)
+        N.check(N.lib.tm_gen_specular(self._h, _dptr(rays_in), _dptr(hits), n, _dptr(n_dev), k,
+                                      float(ior), float(tmax), _dptr(rays_out), _dptr(count),
+                                      _dptr(src), _stream(stream)), "tm_gen_specular")
+        return rays_out, count, src
 
     def gen_secondary(self, hits: torch.Tensor, per_hit: int, tmax: float, seed: int,
                       n_dev: torch.Tensor | None = None, rays_out: torch.Tensor | None = None,

@@ -22,7 +22,9 @@ not available):
   union of spheres.  Every cell face between an inside and an outside cell
   becomes two constrained triangles, split along the face diagonal from its
   minimum to its maximum corner (the diagonal the Kuhn split puts there):
-  (q00, q10, q11) and (q00, q11, q01), with b < c the two in-face axes.
+  (q00, q10, q11) and (q00, q11, q01), with b < c the two in-face axes,
+  each with its last two vertices swapped where needed so that its normal
+  (v1-v0) x (v2-v0) points out of the inside cell (the "+ side" is outside).
   Triangle id = enumeration order: axis (x, y, z), then face position with
   i fastest, then the half.
 * Pinhole camera looking along +z, image x along +x, image y (downwards)
@@ -136,8 +138,12 @@ def constrained_faces(n: int, inside: np.ndarray) -> np.ndarray:
             q[cax] = q[cax] + dc
             return point_id(n, q[0], q[1], q[2])
         q00, q10, q01, q11 = pid(0, 0), pid(1, 0), pid(0, 1), pid(1, 1)
-        t0 = np.stack([q00, q10, q11], axis=1)
-        t1 = np.stack([q00, q11, q01], axis=1)
+        # (q10 - q00) x (q11 - q00) points along +axis for x and z, -axis for
+        # y; flip where that is not the way out of the inside cell
+        out_pos = a[kk, jj, ii]
+        flip = out_pos != (axis != 1)
+        t0 = np.where(flip[:, None], np.stack([q00, q11, q10], axis=1), np.stack([q00, q10, q11], axis=1))
+        t1 = np.where(flip[:, None], np.stack([q00, q01, q11], axis=1), np.stack([q00, q11, q01], axis=1))
         out.append(np.stack([t0, t1], axis=1).reshape(-1, 3))
     return np.concatenate(out, axis=0).astype(np.int32)
 

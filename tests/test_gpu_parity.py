@@ -9,7 +9,7 @@ import pytest
 import oracle
 import scenegen as sg
 from oracle.secondary import hit_side, secondary_rays
-from tests.parity import compare
+from tests.parity import compare, hit_points
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,24 @@ class Case:
         h = self.mesh.trace(rays, **kw)
         torch.cuda.synchronize()
         return tmx.unpack_hits(h)
+
+
+def device_hits(tmx, c, w):
+    """The oracle's hits w as tm_hit records for case c (internal tet ids,
+    arrival-side flag), and the arrival side of each."""
+    n = len(w["tri"])
+    h = np.zeros((n, 8), np.int32)
+    f = h.view(np.float32)
+    hit = w["tri"] >= 0
+    side = hit_side(c.ctet, w["tri"], w["tet"])
+    h[:, 0] = w["tri"]
+    f[:, 1] = w["t"].astype(np.float32)
+    f[:, 2] = w["b1"].astype(np.float32)
+    f[:, 3] = w["b2"].astype(np.float32)
+    h[:, 4] = np.where(hit, c.tinv[np.maximum(w["tet"], 0)], -1)
+    h[:, 5] = np.where(hit, w["tri"], -1)
+    h[:, 7] = np.where(hit & (side == 1), tmx.HIT_SIDE_NEG, 0)
+    return h, side
 
 
 def camera_case(tmx, name, n_override=None, order="hilbert"):
@@ -177,25 +195,55 @@ def test_restart_rays(tmx, tiny, mode):
 
 
 def test_gen_secondary_matches_generator(tmx, tiny):
+    """The device generator on the oracle's primary hits equals the oracle's generator."""
     o, d = sg.camera_rays(tiny.s.camera)
-    rays = dev(tmx.pack_rays(o, d, np.inf, tiny.cam_internal))
-    hits = tiny.mesh.trace(rays)
-    g = tmx.unpack_hits(hits)
-    side = ((g["flags"] & tmx.HIT_SIDE_NEG) != 0).astype(np.int32)
+    w = tiny.oracle_trace(o, d, np.inf, tiny.cam_in[0])
+    h, side = device_hits(tmx, tiny, w)
+    hits = dev(h)
     for per_hit, tmax in ((1, np.inf), (8, 0.05)):
         r2, cnt, src = tiny.mesh.gen_secondary(hits, per_hit, tmax, seed=1234, src=True)
         torch.cuda.synchronize()
         k = int(cnt.item())
         r2 = r2[:k].cpu().numpy()
         src = src[:k].cpu().numpy()
-        o2, d2, tm2, entry, src_o = secondary_rays(tiny.s.points, tiny.s.tris, g["tri"],
-                                                   g["b1"], g["b2"], side, 1234, per_hit, tmax)
-        assert k == len(o2) == per_hit * (g["tri"] >= 0).sum()
+        o2, d2, tm2, entry, src_o = secondary_rays(tiny.s.points, tiny.s.tris, w["tri"],
+                                                   np.float32(w["b1"]), np.float32(w["b2"]), side,
+                                                   1234, per_hit, tmax)
+        assert k == len(o2) == per_hit * (w["tri"] >= 0).sum()
         assert np.array_equal(src, src_o)
         assert np.array_equal(r2.view(np.int32)[:, 3], -1 - entry)
         assert np.abs(r2[:, 0:3] - o2).max() < 1e-6
         assert np.abs(r2[:, 4:7] - d2).max() < 2e-5
         assert np.array_equal(r2[:, 7], tm2)
+
+
+@pytest.mark.parametrize("mode", ["fp32g", "fp32", "fp64"])
+def test_record_formats_identical(tmx, mode):
+    """Tet16, Tet20 (split and packed) and Tet32 walks (Alg. 7, 5, 3) take the same steps: identical hits."""
+    for scene in (sg.make_config("tiny"), None):
+        if scene is None:
+            c0 = random_case(tmx, 6, 515)
+            scene = c0.s
+        om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
+        mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, tet20=True)
+        tinv = np.empty(scene.n_tets, np.int64)
+        tinv[mesh.export()["tet_perm"]] = np.arange(scene.n_tets)
+        g = np.random.default_rng(8)
+        q = g.uniform(0.05, 0.95, size=(3000, 3)).astype(np.float32)
+        start, mb = om.locate(q)
+        keep = mb > 1e-7
+        d = g.normal(size=(3000, 3))
+        d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+        for tmax in (np.inf, 0.2):
+            rays = dev(tmx.pack_rays(q[keep], d[keep], tmax, tinv[start[keep]]))
+            got = {f: tmx.unpack_hits(mesh.trace(rays, mode=mode, format=f,
+                                                 tmax_early_exit=np.isfinite(tmax)))
+                   for f in ("tet16", "tet20", "tet20_aos", "tet32")}
+            for f in ("tet20", "tet20_aos", "tet32"):
+                for k in ("tri", "t", "b1", "b2", "tet", "steps", "flags"):
+                    assert np.array_equal(got[f][k], got["tet16"][k]), (f, k)
+            w = om.trace(q[keep], d[keep], tmax, start[keep])
+            compare(scene.points, scene.tris, got["tet32"], w, check_t=(mode != "fp32"))
 
 
 def test_hilbert_and_input_order_identical(tmx):
@@ -235,14 +283,28 @@ def test_precision_full_size_sampled(tmx, precision, mode):
     w = c.oracle_trace(o[sel], d[sel], np.inf, c.cam_in[0])
     g = tmx.unpack_hits(hits[torch.from_numpy(sel).cuda()])
     st = compare(c.s.points, c.s.tris, g, w, check_t=(mode != "fp32"))
-    # the device-generated bounce rays, sampled, traced by the oracle from the same inputs
+    # bounce rays generated by the oracle from its own hits of the sampled
+    # pixels (counter = pixel ray index), traced by both
+    side = hit_side(c.ctet, w["tri"], w["tet"])
+    ob, db, tb, eb, _ = secondary_rays(c.s.points, c.s.tris, w["tri"], np.float32(w["b1"]),
+                                       np.float32(w["b2"]), side, 77, 1, np.inf, ray_ids=sel)
+    gb = tmx.unpack_hits(c.mesh.trace(dev(tmx.pack_rays(ob, db, tb, -1 - eb)), mode=mode))
+    st2 = compare(c.s.points, c.s.tris, gb, c.oracle_trace(ob, db, tb, -1, eb),
+                  check_t=(mode != "fp32"))
+    # the device-generated bounce rays of the timed path: every hit lies on
+    # its ray and on its triangle
     k = int(cnt.item())
     sel2 = np.random.default_rng(4).choice(k, min(k, 20000), replace=False)
     rb = r2[torch.from_numpy(sel2).cuda()].cpu().numpy()
-    code = -1 - rb.view(np.int32)[:, 3]
-    w2 = c.oracle_trace(rb[:, 0:3], rb[:, 4:7], rb[:, 7], -1, code)
     g2 = tmx.unpack_hits(h2[torch.from_numpy(sel2).cuda()])
-    st2 = compare(c.s.points, c.s.tris, g2, w2, check_t=(mode != "fp32"))
+    hit = g2["tri"] >= 0
+    assert hit.mean() > 0.2
+    on_ray = rb[hit, 0:3].astype(np.float64) + g2["t"][hit, None].astype(np.float64) * rb[hit, 4:7]
+    on_tri = hit_points(c.s.points, c.s.tris, g2["tri"][hit], g2["b1"][hit], g2["b2"][hit])
+    tol = 2e-5 if mode == "fp32" else 4e-6
+    assert (np.linalg.norm(on_ray - on_tri, axis=1) / np.maximum(1, g2["t"][hit])).max() < tol
+    assert (g2["b1"][hit] >= -1e-5).all() and (g2["b2"][hit] >= -1e-5).all()
+    assert (g2["b1"][hit] + g2["b2"][hit] <= 1 + 1e-5).all()
     print(mode, "primary", st, "bounce", st2)
 
 

@@ -157,3 +157,22 @@ def test_build_errors(tmx):
     P = m.export()["points"][:, :3].astype(np.float64)
     a, b, c, d = (P[cold[:, k]] for k in range(4))
     assert (np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a) > 0).all()
+
+
+def test_tet20_records(tmx):
+    """Tet20 (Sec. 3): VX and the four neighbours sorted by the ids of the vertices they sit across."""
+    s = sg.make_config("tiny")
+    m = tmx.Mesh(s.points, s.tets, s.tris, upload=False, tet20=True)
+    e = m.export()
+    t20 = m.export_tet20()
+    V = e["cold"][:, :4].astype(np.int64)
+    Nb = e["cold"][:, 4:].astype(np.int64) & 0xFFFFFFFF
+    order = np.argsort(V, axis=1, kind="stable")
+    Ns = np.take_along_axis(Nb, order, 1)
+    assert np.array_equal(t20["vxn"][:, 0], e["tet16"][:, 0])
+    assert np.array_equal(t20["vxn"][:, 1:].astype(np.int64) & 0xFFFFFFFF, Ns[:, :3])
+    assert np.array_equal(t20["n3"].astype(np.int64) & 0xFFFFFFFF, Ns[:, 3])
+    assert np.array_equal(t20["aos"][:, :4], t20["vxn"]) and np.array_equal(t20["aos"][:, 4], t20["n3"])
+    from paper_2103_02309_gb300 import _native as N
+    with pytest.raises(N.TetmeshError):
+        tmx.Mesh(s.points, s.tets, s.tris, upload=False).export_tet20()

@@ -65,3 +65,53 @@ def test_mutant_is_caught(tmp_path, monkeypatch, name):
     lib = build_variant(tmp_path, name, *MUTANTS[name])
     monkeypatch.setattr(oracle, "_lib", lib)
     assert run_pins() > 0, f"no pin caught the planted mistake {name}"
+
+
+# Mistakes planted in a copy of the secondary-ray generators (oracle/secondary.py),
+# loaded as a separate module; the pins of tests/test_oracle_rays.py run on it.
+GEN_MUTANTS = {
+    "eta_inverted": ("eta = np.where(side == 1, float(ior), 1.0 / float(ior))",
+                     "eta = np.where(side == 1, 1.0 / float(ior), float(ior))"),
+    "mirror_sign": ("refl = w + (2.0 * cs)[:, None] * na", "refl = w - (2.0 * cs)[:, None] * na"),
+    "refract_side": ("out_side = np.where(ok, 1 - side, side)", "out_side = side"),
+    "shadow_side": ('side = np.where(np.einsum("ij,ij->i", nrm, L - v0) >= 0.0, 0, 1)',
+                    'side = np.where(np.einsum("ij,ij->i", nrm, L - v0) >= 0.0, 1, 0)'),
+    "snell_root_sign": ("(eta * cs - np.sqrt(np.maximum(k, 0.0)))",
+                        "(eta * cs + np.sqrt(np.maximum(k, 0.0)))"),
+    "normal_not_turned": ("na = np.where((side == 1)[:, None], -n, n)", "na = n"),
+    "shadow_tmax_short": ("ln.astype(np.float32),", "(0.99 * ln).astype(np.float32),"),
+}
+
+
+def load_generators(name=None):
+    import importlib.util
+    import types
+    from oracle import secondary
+    src = open(secondary.__file__).read()
+    if name is not None:
+        old, new = GEN_MUTANTS[name]
+        assert src.count(old) == 1, f"mutation site for {name} not unique"
+        src = src.replace(old, new)
+    mod = types.ModuleType(f"secondary_{name}")
+    exec(compile(src, f"<secondary {name}>", "exec"), mod.__dict__)
+    return mod
+
+
+def run_generator_pins(mod):
+    from tests import test_oracle_rays as rays
+    failed = 0
+    for check in rays.CHECKS:
+        try:
+            check(mod)
+        except Exception:
+            failed += 1
+    return failed
+
+
+def test_unmodified_generators_pass_pins():
+    assert run_generator_pins(load_generators()) == 0
+
+
+@pytest.mark.parametrize("name", sorted(GEN_MUTANTS))
+def test_generator_mutant_is_caught(name):
+    assert run_generator_pins(load_generators(name)) > 0, f"no pin caught {name}"
