@@ -13,6 +13,15 @@ same step on the same inputs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Other measurements on the same step (each prints its own JSON line):
+  --workload medium|large|tiny|batched   other scene sizes (large: 8 AO rays per hit)
+  --order hilbert|input|hilbert_regions  memory order of the mesh (Sec. 5)
+  --format tet16|tet20|tet20_aos|tet32   tet record the walk reads (Sec. 3)
+  --secondary bounce|ao|shadow|reflect|refract
+                                         the rays generated from the primary hits
+                                         (Sec. 6; shadow rays go to a point light
+                                         located on the device every step)
+
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -39,11 +48,16 @@ FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 RAY_BYTES, HIT_BYTES = 32, 32
 # Algorithmic bytes of the walk kernel (the dominant kernel): per tet step one
-# Tet16 record and one float4 point; per ray its start record (32 B, in the
-# hit slot), the ray (32 B), the three entry-face points (48 B) and the end
-# record (32 B).
-STEP_BYTES = 16 + 16
+# tet record (RECORD_BYTES of the format the walk reads) and one float4
+# point; per ray its start record (32 B, in the hit slot), the ray (32 B),
+# the three entry-face points (48 B) and the end record (32 B).
 WALK_RAY_BYTES = 32 + RAY_BYTES + 3 * 16 + 32
+RECORD_BYTES = {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32}
+# Rays generated from each hit: (rays per hit, tmax); None = per-ray (shadow)
+SECONDARY = {"bounce": (1, float("inf")), "ao": (8, 0.05), "shadow": (1, None),
+             "reflect": (1, float("inf")), "refract": (1, float("inf"))}
+LIGHT = (0.3, 0.75, 0.05)   # point light of the shadow measurement (inside the unit cube)
+IOR = 1.5                   # refractive index of the inside of the spheres
 
 WORKLOADS = {
     "tiny": dict(desc="8^3-cell Kuhn grid (3,072 tets), one sphere, 64x64 primary rays + 1 cosine "
@@ -70,7 +84,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="precision")
-    p.add_argument("--order", choices=["hilbert", "input"], default="hilbert")
+    p.add_argument("--order", choices=["hilbert", "input", "hilbert_regions"], default="hilbert")
+    p.add_argument("--format", choices=sorted(RECORD_BYTES), default="tet32",
+                   help="tet record the walk reads (tet32 is the library's automatic choice)")
+    p.add_argument("--secondary", choices=sorted(SECONDARY), default=None,
+                   help="rays generated from the primary hits (default: the workload's)")
     p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
@@ -105,8 +123,10 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
+def profiled_traffic(workload, variant=""):
     """DRAM bytes per trace launch from the committed ncu summary, if it matches the source."""
+    if variant:
+        return None
     path = os.path.join(ROOT, "profiles", f"walk_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -198,14 +218,21 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     from paper_2103_02309_gb300 import tetmesh as tmx
 
-    W = WORKLOADS[args.workload]
+    W = dict(WORKLOADS[args.workload])
+    kind = args.secondary or W["kind"]
+    if kind != W["kind"]:
+        W["per_hit"], W["tmax"] = SECONDARY[kind]
+        W["kind"] = kind
     s = build_scene(args.workload)
     t0 = time.time()
-    mesh = tmx.Mesh(s.points, s.tets, s.tris, order=args.order)
+    mesh = tmx.Mesh(s.points, s.tets, s.tris, order=args.order,
+                    tet20=args.format.startswith("tet20"))
     build_s = time.time() - t0
     cam = tmx.make_camera(s.camera.eye, s.camera.fov_deg, s.camera.width, s.camera.height)
     n_primary = s.camera.width * s.camera.height
     per_hit = W["per_hit"]
+    default_run = (kind == WORKLOADS[args.workload]["kind"] and args.format == "tet32"
+                   and args.order == "hilbert")
     dev = torch.device("cuda", local)
     eye = torch.tensor([s.camera.eye], dtype=torch.float32, device=dev)
     start = torch.empty(1, dtype=torch.int32, device=dev)
@@ -214,6 +241,8 @@ def run_ours(args, world, rank, local):
     rays2 = torch.empty((n_primary * per_hit, 8), dtype=torch.float32, device=dev)
     hits2 = torch.empty((n_primary * per_hit, 8), dtype=torch.int32, device=dev)
     count = torch.empty(1, dtype=torch.int64, device=dev)
+    light = torch.tensor([LIGHT], dtype=torch.float32, device=dev)
+    light_tet = torch.empty(1, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -224,16 +253,26 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
 
     def opts(mode, ev=None):
+        bounded = W["tmax"] is not None and math.isfinite(W["tmax"])
         return tmx.trace_opts(mode=mode, block=args.block, refill=args.refill,
-                              batch_steps=args.batch_steps, tmax_early_exit=math.isfinite(W["tmax"]),
-                              phase_events=ev)
+                              batch_steps=args.batch_steps, tmax_early_exit=bounded,
+                              phase_events=ev, format=args.format)
 
     def step(op, ob):
         mesh.locate(eye, out=start)
+        if kind == "shadow":
+            mesh.locate(light, out=light_tet)          # the point light, once per frame
         tmx.gen_primary(cam, start, rays=rays)
         mesh.trace(rays, hits=hits, opts=op)
-        mesh.gen_secondary(hits, per_hit, W["tmax"], seed=0x5EED, rays_out=rays2, count=count)
-        mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
+        if kind in ("bounce", "ao"):
+            mesh.gen_secondary(hits, per_hit, W["tmax"], seed=0x5EED, rays_out=rays2, count=count)
+            mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
+        elif kind == "shadow":
+            mesh.gen_shadow(hits, LIGHT, rays_out=rays2, count=count)
+            mesh.trace_shadow(rays2, light_tet, hits=hits2, n_dev=count, opts=ob)
+        else:
+            mesh.gen_specular(rays, hits, kind, IOR, rays_out=rays2, count=count)
+            mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
 
     def timed(mode, steps, warmup):
         op, ob = opts(mode, ev_p), opts(mode, ev_b)
@@ -272,21 +311,29 @@ def run_ours(args, world, rank, local):
     g1 = tmx.unpack_hits(hits)
     g2 = tmx.unpack_hits(hits2[:n_second])
     steps_total = int(g1["steps"].astype(np.int64).sum() + g2["steps"].astype(np.int64).sum())
-    alg_bytes = steps_total * STEP_BYTES + rays_per_step * WALK_RAY_BYTES
+    step_bytes = RECORD_BYTES[args.format] + 16
+    alg_bytes = steps_total * step_bytes + rays_per_step * WALK_RAY_BYTES
     guard_rate = float(((g1["flags"] & tmx.HIT_GUARD) != 0).mean())
     fl = np.concatenate([g1["flags"], g2["flags"]])
     slow_rate = float(((fl & tmx.HIT_SLOW_PASS) != 0).mean())
     final64_rate = float(((np.concatenate([g1["flags"], g2["flags"]]) & tmx.HIT_FINAL_FP64) != 0).mean())
     value = world * rays_per_step / (ms * 1e-3) / 1e6
+    extra = {}
+    if kind == "shadow":
+        extra = {"light": LIGHT, "light_tet": int(light_tet.item()),
+                 "lit_rate": float(((g2["flags"] & tmx.HIT_REACHED) != 0).mean()) if n_second else 0.0}
+    elif kind in ("reflect", "refract"):
+        extra = {"ior": IOR, "secondary_hit_rate": float((g2["tri"] >= 0).mean()) if n_second else 0.0}
 
     hbm, hbm_src = measured_hbm()
     achieved = alg_bytes / (walk_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload, "" if default_run else "variant")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "walk_kernel (primary + bounce launches; bytes and time per step)",
+                "kernel": f"walk_kernel (primary + {kind} launches; bytes and time per step)",
+                "bytes_per_tet_step": step_bytes,
                 "algorithmic_bytes_per_launch": alg_bytes // 2,
                 "walk_ms_per_launch": round(walk_ms / 2, 4),
                 "tet_steps_per_step": steps_total,
@@ -308,27 +355,29 @@ def run_ours(args, world, rank, local):
         hits.copy_(keep[0])
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and kind in ("bounce", "ao"):
         e2e = run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world)
 
     cpu = None
-    if not args.no_cpu and world == 1 and rank == 0:
+    if not args.no_cpu and world == 1 and rank == 0 and kind in ("bounce", "ao"):
         cpu = cpu_baseline(args.workload, s, W, budget_s=20.0)
 
     if rank == 0:
+        metric = METRIC if kind == WORKLOADS[args.workload]["kind"] else f"Mrays/s (primary + {kind})"
         line = {
-            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "metric": metric, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {W['desc']}", "mode": "FP32 walk + FP64 guard",
                        "tets": s.n_tets, "points": s.n_points, "triangles": s.n_tris,
                        "rays_per_step": rays_per_step, "primary": n_primary, "secondary": n_second,
-                       "order": args.order, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "order": args.order, "format": args.format, "secondary": kind,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between steps (256 MiB write outside the step events)",
                        "build_s": round(build_s, 2),
                        "guard_rate_primary": guard_rate, "slow_pass_rate": slow_rate,
-                       "final_fp64_rate": final64_rate},
+                       "final_fp64_rate": final64_rate, **extra},
             "roofline": roofline, "arms": arms, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
         }
@@ -532,7 +581,8 @@ def run_batched(args, world, rank, local):
             "config": {"workload": f"batched: {WORKLOADS['batched']['desc']}", "rays": total,
                        "meshes": len(meshes), "tets": int(sum(m.n_tets for m in meshes)),
                        "build_s": round(build_s, 1),
-                       "autotuned": {"block": tuned.opts.block, "refill": tuned.opts.refill,
+                       "autotuned": {"format": {v: k for k, v in tmx.FORMATS.items()}[tuned.opts.format],
+                                     "block": tuned.opts.block, "refill": tuned.opts.refill,
                                      "batch_steps": tuned.opts.batch_steps,
                                      "sort_chunk": tuned.sort_chunk, "ms": round(tuned.ms, 3)}},
             "separate_launches": {"value": round(total / (ms_sep * 1e-3) / 1e6, 2),

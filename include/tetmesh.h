@@ -62,16 +62,34 @@ enum {
     TM_MODE_FP64 = 2        /* FP64 projections and sign tests throughout */
 };
 
-enum { TM_ORDER_HILBERT = 0, TM_ORDER_INPUT = 1 };
+/* Memory order of points and tets (Sec. 5): TM_ORDER_HILBERT sorts points
+ * by the Hilbert key of their position and tets by that of their centroid;
+ * TM_ORDER_INPUT keeps the input order; TM_ORDER_HILBERT_REGIONS sorts the
+ * points the same way and the tets first by region, then by Hilbert key.  A
+ * region is a maximal set of tets connected through faces that are not
+ * constrained (a walk never leaves its region); regions are ordered by the
+ * smallest Hilbert key of their tets. */
+enum { TM_ORDER_HILBERT = 0, TM_ORDER_INPUT = 1, TM_ORDER_HILBERT_REGIONS = 2 };
 
 /* Tet record the walk reads (Sec. 3): Tet16 = VX and NX_j = N_j ^ N_3
- * (16 B, the default, decoded with the previous tet, Alg. 7); Tet20 = VX and
- * N_0..N_3 sorted by the ids of the vertices they sit across (20 B, Alg. 5;
- * needs tm_build_opts.tet20), stored split (TM_FORMAT_TET20: a 16-B
+ * (16 B, decoded with the previous tet, Alg. 7); Tet20 = VX and N_0..N_3
+ * sorted by the ids of the vertices they sit across (20 B, Alg. 5; needs
+ * tm_build_opts.tet20), stored split (TM_FORMAT_TET20: a 16-B
  * {VX, N0, N1, N2} array and a 4-B N3 array) or packed (TM_FORMAT_TET20_AOS:
  * one int32[5] per tet at a 20-B stride); Tet32 = the full record V0..V3,
- * N0..N3 (32 B, the mesh's cold records; Alg. 3 with VX = V0^V1^V2^V3). */
-enum { TM_FORMAT_TET16 = 0, TM_FORMAT_TET20 = 1, TM_FORMAT_TET32 = 2, TM_FORMAT_TET20_AOS = 3 };
+ * N0..N3 (32 B, the mesh's cold records, so it needs no extra memory; Alg. 3
+ * with VX = V0^V1^V2^V3).  All give identical hits.  TM_FORMAT_AUTO (0)
+ * selects Tet32: on GB300 the walk is bound by instruction issue, not by
+ * memory, a 32-byte record costs one 32-byte sector like a 16-byte one, and
+ * the full record needs the fewest instructions to decode.  Batches take
+ * Tet16, Tet32 or packed Tet20. */
+enum {
+    TM_FORMAT_AUTO = 0,
+    TM_FORMAT_TET16 = 1,
+    TM_FORMAT_TET20 = 2,
+    TM_FORMAT_TET32 = 3,
+    TM_FORMAT_TET20_AOS = 4
+};
 
 /* A ray, 32 bytes, two 16-byte words.
  *   start >= 0 : internal id of a tet that holds the origin (o).
@@ -118,7 +136,7 @@ typedef struct {
                                      constrained triangle in between); reported as a miss */
 
 typedef struct {
-    int32_t order;           /* TM_ORDER_HILBERT (default) or TM_ORDER_INPUT */
+    int32_t order;           /* TM_ORDER_* (default TM_ORDER_HILBERT) */
     int32_t fix_orientation; /* nonzero: swap V2,V3 of tets with orient3d < 0 instead of failing */
     int32_t tet20;           /* nonzero: also pack the Tet20 records, split and packed (40 B per tet) */
 } tm_build_opts;
@@ -136,7 +154,7 @@ typedef struct {
     void *phase_events[4];   /* optional cudaEvent_t handles recorded on the stream before the
                                 start phase, after it, after the walk and after the finish
                                 phase (tm_trace only); NULL entries are skipped */
-    int32_t format;          /* TM_FORMAT_*: the record the walk reads (batches: Tet16 only) */
+    int32_t format;          /* TM_FORMAT_*: the record the walk reads (0: auto) */
 } tm_trace_opts;
 
 /* Mesh description returned by tm_mesh_info.  Device pointers are owned by
@@ -155,6 +173,7 @@ typedef struct {
     const void *tet20_n3_dev;    /* int32[n_tets] N3, or NULL */
     const void *tet20_aos_dev;   /* int32[5*n_tets] (VX, N0, N1, N2, N3), or NULL */
     int64_t device_bytes;        /* bytes the mesh holds on the device */
+    int64_t n_regions;           /* regions found by TM_ORDER_HILBERT_REGIONS, else 0 */
 } tm_mesh_info;
 
 /* Builds the compact mesh (Sec. 3) from HOST arrays, which are copied:
@@ -227,15 +246,18 @@ tm_status tm_trace(const tm_mesh *mesh, const tm_ray *rays, int64_t n, const int
 
 /* Shadow rays toward a point light (Sec. 6): the walk of tm_trace, which
  * also ends, as a miss flagged TM_HIT_REACHED, when it enters (or starts in)
- * the tet light_tet that holds the light (internal id, e.g. from
- * tm_locate).  A hit (tri >= 0) is the nearest constrained triangle between
- * the origin and the light: the light is occluded.  Each ray's tmax should
- * be its distance to the light (in units of |d|): a walk that passes the
- * light's tet by rounding then still ends, as a miss without the flag,
- * once its entry face lies beyond tmax (opts->tmax_early_exit is implied).
- * Arguments as tm_trace; TM_ERR_ARG if light_tet is not a tet of the mesh. */
+ * the tet that holds the light: *light_tet_dev (DEVICE int32, internal id,
+ * e.g. written by tm_locate for the light at the start of the frame, so no
+ * host round trip is needed).  A hit (tri >= 0) is the nearest constrained
+ * triangle between the origin and the light: the light is occluded.  Each
+ * ray's tmax should be its distance to the light (in units of |d|): a walk
+ * that passes the light's tet by rounding then still ends, as a miss
+ * without the flag, once its entry face lies beyond tmax
+ * (opts->tmax_early_exit is implied).  A light tet id outside the mesh
+ * (e.g. -1 from tm_locate for a light outside it) disables the stop.
+ * Other arguments as tm_trace. */
 tm_status tm_trace_shadow(const tm_mesh *mesh, const tm_ray *rays, int64_t n,
-                          const int64_t *n_dev, int32_t light_tet, tm_hit *hits,
+                          const int64_t *n_dev, const int32_t *light_tet_dev, tm_hit *hits,
                           const tm_trace_opts *opts, void *stream);
 
 /* Pinhole camera of the synthetic workloads: eye, looking along +z, image x
@@ -328,7 +350,7 @@ tm_status tm_gen_secondary_noalloc(const tm_mesh *mesh, const tm_hit *hits, int6
  *   descriptor table is uploaded synchronously and the graph is rebuilt.
  * tm_batch_run: replays the graph on `stream` (sort + trace).
  * tm_batch_run_separate: the same work as one tm_trace launch per mesh.
- * tm_batch_autotune: times candidate (block, refill, batch_steps,
+ * tm_batch_autotune: times candidate (format, block, refill, batch_steps,
  *   sort_chunk) settings on the current rays, keeps the fastest, and writes
  *   it to *best (may be NULL); sort_chunk 0 disables the ray sort. */
 tm_status tm_batch_create(const tm_mesh *const *meshes, int n_meshes, tm_batch **out);

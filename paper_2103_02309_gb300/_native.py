@@ -55,7 +55,7 @@ class MeshInfo(ctypes.Structure):
                 ("bbox_lo", f32 * 3), ("bbox_hi", f32 * 3), ("source_tet", i32),
                 ("on_device", i32), ("tet16_dev", P), ("points_dev", P), ("cold_dev", P),
                 ("cface_dev", P), ("tet20_dev", P), ("tet20_n3_dev", P), ("tet20_aos_dev", P),
-                ("device_bytes", i64)]
+                ("device_bytes", i64), ("n_regions", i64)]
 
 
 class Camera(ctypes.Structure):
@@ -78,7 +78,7 @@ _SIGS = {
     "tm_hilbert_keys": ([P, i64, ctypes.c_int, P], ctypes.c_int),
     "tm_locate": ([P, P, i64, P, i32, P, P], ctypes.c_int),
     "tm_trace": ([P, P, i64, P, P, ctypes.POINTER(TraceOpts), P], ctypes.c_int),
-    "tm_trace_shadow": ([P, P, i64, P, ctypes.c_int32, P, ctypes.POINTER(TraceOpts), P], ctypes.c_int),
+    "tm_trace_shadow": ([P, P, i64, P, P, P, ctypes.POINTER(TraceOpts), P], ctypes.c_int),
     "tm_gen_primary": ([ctypes.POINTER(Camera), P, f32, P, P], ctypes.c_int),
     "tm_gen_secondary": ([P, P, i64, P, ctypes.c_int, f32, u64, P, P, P, P], ctypes.c_int),
     "tm_gen_shadow": ([P, P, i64, P, f32, f32, f32, P, P, P, P], ctypes.c_int),

@@ -193,6 +193,10 @@ tm_status tm_batch_set(tm_batch *b, const tm_ray *const *rays, const int64_t *n,
         b->cursor_bytes = batch_scratch_bytes(offset);
     }
     b->cfg = resolve_trace_opts(opts, max_nt);
+    if (b->cfg.format == TM_FORMAT_TET20) return TM_ERR_ARG;  // two arrays per mesh: not batched
+    if (b->cfg.format == TM_FORMAT_TET20_AOS)
+        for (const tm_mesh *m : b->meshes)
+            if (!m->d_t20aos) return TM_ERR_ARG;
     b->sort_chunk = sort_chunk;
     b->n_chunks = (int64_t)chunks.size();
     if (b->n_chunks > b->chunks_cap) {
@@ -246,6 +250,7 @@ tm_status tm_batch_autotune(tm_batch *b, int reps, tm_tuned *best, void *stream)
     o.block = b->cfg.block;
     o.refill = b->cfg.refill;
     o.batch_steps = b->cfg.batch_steps;
+    o.format = b->cfg.format;
     int32_t chunk = b->sort_chunk;
     auto measure = [&](const tm_trace_opts &opt, int32_t sc, float *ms) -> tm_status {
         tm_status st = tm_batch_set(b, rays.data(), n.data(), hits.data(), &opt, sc);
@@ -266,8 +271,15 @@ tm_status tm_batch_autotune(tm_batch *b, int reps, tm_tuned *best, void *stream)
     const int refills[] = {4, 8, 16, 24, 32};
     const int steps[] = {2, 4, 8, 16, 32};
     const int chunks[] = {0, 256, 1024, 4096};
+    const int formats[] = {TM_FORMAT_TET32, TM_FORMAT_TET16};
     for (int pass = 0; pass < 2 && st == TM_OK; ++pass) {
+        for (int v : formats) {
+            tm_trace_opts c = o; c.format = v; float ms;
+            if ((st = measure(c, chunk, &ms)) != TM_OK) break;
+            if (ms < best_ms) { best_ms = ms; o = c; }
+        }
         for (int v : blocks) {
+            if (st != TM_OK) break;
             tm_trace_opts c = o; c.block = v; float ms;
             if ((st = measure(c, chunk, &ms)) != TM_OK) break;
             if (ms < best_ms) { best_ms = ms; o = c; }

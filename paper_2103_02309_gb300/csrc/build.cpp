@@ -10,7 +10,9 @@
 //     the tet whose opposite vertex lies on the + side of the triangle's own
 //     plane becomes tet+, the other tet-;
 //  4. Hilbert keys (3 x 21 bits) of point positions and tet centroids, a
-//     stable sort, and the renumbering of every id;
+//     stable sort, and the renumbering of every id; with regions (Sec. 5),
+//     the tets are first grouped by the connected component of the
+//     non-constrained face graph that holds them (a concurrent union-find);
 //  5. packing: cold records (V0..V3, N0..N3) and Tet16 records
 //     (VX = V0^V1^V2^V3; NX_j = N_j ^ N_3 with the neighbours sorted by the
 //     id of the vertex they sit across, Sec. 3 "Tet20"/"Tet16").
@@ -105,6 +107,67 @@ void hilbert_order(const std::vector<uint64_t> &key, std::vector<int32_t> &perm)
     for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = kv[(size_t)i].second;
 }
 
+// Concurrent union-find over tet ids: a root is a self-parent; union links
+// the larger root below the smaller one with a compare-and-swap, find halves
+// the path as it goes.  Used to label the regions of Sec. 5.
+struct UnionFind {
+    std::vector<std::atomic<int32_t>> parent;
+    explicit UnionFind(int64_t n) : parent((size_t)n) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) parent[(size_t)i].store((int32_t)i, std::memory_order_relaxed);
+    }
+    int32_t find(int32_t x) {
+        for (;;) {
+            int32_t p = parent[(size_t)x].load(std::memory_order_relaxed);
+            if (p == x) return x;
+            const int32_t g = parent[(size_t)p].load(std::memory_order_relaxed);
+            if (g != p) parent[(size_t)x].compare_exchange_weak(p, g, std::memory_order_relaxed);
+            x = g;
+        }
+    }
+    void unite(int32_t a, int32_t b) {
+        for (;;) {
+            a = find(a);
+            b = find(b);
+            if (a == b) return;
+            if (a < b) std::swap(a, b);
+            int32_t expect = a;
+            if (parent[(size_t)a].compare_exchange_strong(expect, b, std::memory_order_acq_rel)) return;
+        }
+    }
+};
+
+// Region of every tet (Sec. 5): 0..n_regions-1, numbered in the order of
+// the smallest Hilbert key (key[t]) among their tets.
+std::vector<int32_t> region_rank(const std::vector<uint32_t> &N, const std::vector<uint64_t> &key,
+                                 int64_t nt) {
+    UnionFind uf(nt);
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t t = 0; t < nt; ++t)
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t nb = N[(size_t)(4 * t + k)];
+            if (!(nb & TM_CFACE_FLAG) && (int64_t)nb > t) uf.unite((int32_t)t, (int32_t)nb);
+        }
+    std::vector<int32_t> root((size_t)nt);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nt; ++t) root[(size_t)t] = uf.find((int32_t)t);
+    // smallest key per root (roots are tet ids), then the roots in key order
+    std::vector<uint64_t> kmin((size_t)nt, ~0ull);
+    for (int64_t t = 0; t < nt; ++t) {
+        uint64_t &k = kmin[(size_t)root[(size_t)t]];
+        if (key[(size_t)t] < k) k = key[(size_t)t];
+    }
+    std::vector<std::pair<uint64_t, int32_t>> roots;
+    for (int64_t t = 0; t < nt; ++t)
+        if (root[(size_t)t] == t) roots.push_back({kmin[(size_t)t], (int32_t)t});
+    std::sort(roots.begin(), roots.end());
+    std::vector<int32_t> rank_of_root((size_t)nt, -1);
+    for (size_t r = 0; r < roots.size(); ++r) rank_of_root[(size_t)roots[r].second] = (int32_t)r;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nt; ++t) root[(size_t)t] = rank_of_root[(size_t)root[(size_t)t]];
+    return root;
+}
+
 inline uint32_t quantise(double v, double lo, double scale) {
     double q = std::floor((v - lo) * scale);
     if (q < 0) q = 0;
@@ -119,7 +182,8 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
     const int order = opts ? opts->order : TM_ORDER_HILBERT;
     const bool fix = opts ? opts->fix_orientation != 0 : false;
     const bool want_t20 = opts ? opts->tet20 != 0 : false;
-    if (order != TM_ORDER_HILBERT && order != TM_ORDER_INPUT) return TM_ERR_ARG;
+    if (order != TM_ORDER_HILBERT && order != TM_ORDER_INPUT && order != TM_ORDER_HILBERT_REGIONS)
+        return TM_ERR_ARG;
     m->np = np;
     m->nt = nt;
     m->nc = nc;
@@ -265,7 +329,7 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
     // 4. Hilbert order --------------------------------------------------------------
     m->pperm.resize((size_t)np);
     m->tperm.resize((size_t)nt);
-    if (order == TM_ORDER_HILBERT) {
+    if (order == TM_ORDER_HILBERT || order == TM_ORDER_HILBERT_REGIONS) {
         const double span = m->extent > 0 ? m->extent : 1.0;
         const double scale = 2097152.0 / span;
         std::vector<uint64_t> key((size_t)np);
@@ -285,7 +349,21 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
                                          quantise(0.25 * c[1], lo[1], scale),
                                          quantise(0.25 * c[2], lo[2], scale), 21);
         }
-        hilbert_order(key, m->tperm);
+        if (order == TM_ORDER_HILBERT_REGIONS) {
+            // tets sorted by (region, Hilbert key, input id)
+            const std::vector<int32_t> reg = region_rank(N, key, nt);
+            std::vector<std::pair<std::pair<int32_t, uint64_t>, int32_t>> kv((size_t)nt);
+#pragma omp parallel for schedule(static)
+            for (int64_t t = 0; t < nt; ++t) kv[(size_t)t] = {{reg[(size_t)t], key[(size_t)t]}, (int32_t)t};
+            __gnu_parallel::sort(kv.begin(), kv.end());
+#pragma omp parallel for schedule(static)
+            for (int64_t t = 0; t < nt; ++t) m->tperm[(size_t)t] = kv[(size_t)t].second;
+            int32_t nreg = 0;
+            for (int64_t t = 0; t < nt; ++t) nreg = std::max(nreg, reg[(size_t)t] + 1);
+            m->n_regions = nreg;
+        } else {
+            hilbert_order(key, m->tperm);
+        }
     } else {
         for (int64_t i = 0; i < np; ++i) m->pperm[(size_t)i] = (int32_t)i;
         for (int64_t t = 0; t < nt; ++t) m->tperm[(size_t)t] = (int32_t)t;

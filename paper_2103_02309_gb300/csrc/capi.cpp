@@ -102,6 +102,7 @@ tm_status tm_mesh_info_get(const tm_mesh *m, tm_mesh_info *info) {
     info->tet20_n3_dev = m->d_t20n3;
     info->tet20_aos_dev = m->d_t20aos;
     info->device_bytes = m->device_bytes;
+    info->n_regions = m->n_regions;
     return TM_OK;
 }
 
@@ -167,16 +168,16 @@ tm_status tm_trace(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_
 }
 
 tm_status tm_trace_shadow(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_t *n_dev,
-                          int32_t light_tet, tm_hit *hits, const tm_trace_opts *opts, void *stream) {
-    if (!m || n < 0 || (n > 0 && (!rays || !hits))) return TM_ERR_ARG;
+                          const int32_t *light_tet_dev, tm_hit *hits, const tm_trace_opts *opts,
+                          void *stream) {
+    if (!m || n < 0 || !light_tet_dev || (n > 0 && (!rays || !hits))) return TM_ERR_ARG;
     if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
-    if (light_tet < 0 || light_tet >= m->nt) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     TraceConfig cfg = resolve_trace_opts(opts, m->nt);
     if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
     if (cfg.format == TM_FORMAT_TET20_AOS && !m->d_t20aos) return TM_ERR_ARG;
     cfg.bounded = true;
-    cfg.stop_tet = light_tet;
+    cfg.stop_tet = light_tet_dev;
     return launch_trace(mesh_view(m), rays, n, n_dev, hits, cfg, (cudaStream_t)stream);
 }
 

@@ -43,6 +43,7 @@ struct tm_mesh {
     int32_t *d_t20n3 = nullptr;
     int32_t *d_t20aos = nullptr;
     int64_t device_bytes = 0;
+    int64_t n_regions = 0;  // regions found by TM_ORDER_HILBERT_REGIONS (else 0)
 };
 
 // Point location starts from the located tet of the nearest lattice point
@@ -109,7 +110,7 @@ struct TraceConfig {
     bool bounded;
     cudaEvent_t events[4];
     int format;
-    int32_t stop_tet;  // point-light rays: stop on entering this tet (-1: none); needs bounded
+    const int32_t *stop_tet;  // point-light rays: DEVICE id of the tet to stop in (null: none); needs bounded
 };
 TraceConfig resolve_trace_opts(const tm_trace_opts *opts, int64_t nt);
 

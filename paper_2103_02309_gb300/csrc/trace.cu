@@ -72,9 +72,16 @@ __device__ __forceinline__ Slot find_slot(const BatchDesc *d, int n_meshes, unsi
 struct PhaseParams {
     int64_t n_cap;
     const int64_t *n_dev;
-    float tau_rel;    // sign-test guard threshold relative to the mesh extent
-    int32_t stop_tet; // point-light rays: the tet that holds the light, else -1
+    float tau_rel;             // sign-test guard threshold relative to the mesh extent
+    const int32_t *stop_tet;   // point-light rays: DEVICE id of the light's tet, else null
 };
+
+// The light's tet of a shadow launch, or -1 (none, or not a tet of the mesh).
+__device__ __forceinline__ int32_t load_stop(const int32_t *p, int32_t nt) {
+    if (!p) return -1;
+    const int32_t t = __ldg(p);
+    return (t >= 0 && t < nt) ? t : -1;
+}
 
 __device__ __forceinline__ int64_t ray_count(const PhaseParams &P) {
     return P.n_dev ? min(P.n_cap, *P.n_dev) : P.n_cap;
@@ -213,6 +220,7 @@ start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
              tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
              const __grid_constant__ PhaseParams P) {
     const int64_t n = ray_count(P);
+    const int32_t stop = MULTI ? -1 : load_stop(P.stop_tet, mv0.nt);
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         if (MULTI) {
@@ -220,7 +228,7 @@ start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
             const BatchDesc &D = descs[s.m];
             start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel, -1);
         } else {
-            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, P.stop_tet);
+            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, stop);
         }
     }
 }
@@ -329,12 +337,21 @@ template <class R> struct Depth<R, true> {
 // One tet record in the walk's format, and the decode of the neighbour across
 // the exit vertex ie (Sec. 3 and Alg. 3, 5, 7).  i0..i2 are the entry face,
 // i3 the new vertex; prev is the tet the walk came from.
+// `base` is the format's record array of the mesh (rec_base); the split
+// Tet20 layout also reads its second array from the mesh view.
 template <int FMT> struct TetRec;
+
+template <int FMT> __device__ __forceinline__ const int4 *rec_base(const MeshView &mv) {
+    return FMT == TM_FORMAT_TET32 ? mv.cold
+         : FMT == TM_FORMAT_TET20 ? mv.t20
+         : FMT == TM_FORMAT_TET20_AOS ? reinterpret_cast<const int4 *>(mv.t20aos)
+                                      : mv.tet16;
+}
 
 template <> struct TetRec<TM_FORMAT_TET16> {  // VX, NX_j = N_j ^ N_3, neighbours by vertex rank
     int4 r;
-    __device__ __forceinline__ void load(const MeshView &, const int4 *tet16, int32_t t) {
-        r = __ldg(tet16 + t);
+    __device__ __forceinline__ void load(const MeshView &, const int4 *base, int32_t t) {
+        r = __ldg(base + t);
     }
     __device__ __forceinline__ int32_t vx() const { return r.x; }
     __device__ __forceinline__ uint32_t next(int32_t prev, int32_t i0, int32_t i1, int32_t i2,
@@ -350,8 +367,8 @@ template <> struct TetRec<TM_FORMAT_TET16> {  // VX, NX_j = N_j ^ N_3, neighbour
 template <> struct TetRec<TM_FORMAT_TET20> {  // VX, N_0..N_3 by vertex rank
     int4 r;
     int32_t n3;
-    __device__ __forceinline__ void load(const MeshView &mv, const int4 *, int32_t t) {
-        r = __ldg(mv.t20 + t);
+    __device__ __forceinline__ void load(const MeshView &mv, const int4 *base, int32_t t) {
+        r = __ldg(base + t);
         n3 = __ldg(mv.t20n3 + t);
     }
     __device__ __forceinline__ int32_t vx() const { return r.x; }
@@ -364,8 +381,8 @@ template <> struct TetRec<TM_FORMAT_TET20> {  // VX, N_0..N_3 by vertex rank
 
 template <> struct TetRec<TM_FORMAT_TET20_AOS> {  // the same, packed at a 20-byte stride
     int32_t vx_, n[4];
-    __device__ __forceinline__ void load(const MeshView &mv, const int4 *, int32_t t) {
-        const int32_t *p = mv.t20aos + 5 * (int64_t)t;
+    __device__ __forceinline__ void load(const MeshView &, const int4 *base, int32_t t) {
+        const int32_t *p = reinterpret_cast<const int32_t *>(base) + 5 * (int64_t)t;
         vx_ = __ldg(p);
         n[0] = __ldg(p + 1);
         n[1] = __ldg(p + 2);
@@ -382,9 +399,9 @@ template <> struct TetRec<TM_FORMAT_TET20_AOS> {  // the same, packed at a 20-by
 
 template <> struct TetRec<TM_FORMAT_TET32> {  // V_0..V_3 and N_j across V_j (the cold record)
     int4 v, nb;
-    __device__ __forceinline__ void load(const MeshView &mv, const int4 *, int32_t t) {
-        v = __ldg(mv.cold + 2 * t);
-        nb = __ldg(mv.cold + 2 * t + 1);
+    __device__ __forceinline__ void load(const MeshView &, const int4 *base, int32_t t) {
+        v = __ldg(base + 2 * t);
+        nb = __ldg(base + 2 * t + 1);
     }
     __device__ __forceinline__ int32_t vx() const { return v.x ^ v.y ^ v.z ^ v.w; }
     __device__ __forceinline__ uint32_t next(int32_t, int32_t, int32_t, int32_t, int32_t,
@@ -401,7 +418,7 @@ struct WalkParams {
     float tau_rel;
     int refill;
     int batch_steps;
-    int32_t stop_tet;  // point-light rays (bounded walks only): the light's tet, else -1
+    const int32_t *stop_tet;  // point-light rays (bounded walks only): DEVICE light tet, else null
 };
 
 // Guard mode: one step of a parked ray, with the double-precision re-test of
@@ -438,7 +455,7 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
     S.m1 = guard_mag(S.p1, sc.tau);
     S.m2 = guard_mag(S.p2, sc.tau);
     TetRec<FMT> rec;
-    rec.load(mv, mv.tet16, S.tet);
+    rec.load(mv, rec_base<FMT>(mv), S.tet);
     const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.vx();
     if ((uint32_t)i3 >= (uint32_t)mv.np) {
         put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
@@ -479,9 +496,11 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
 }
 
 // Register budget per thread of the walk (float32; the FP64 arm keeps
-// double-width state).  Set by measurement on GB300.
+// double-width state).  Set by measurement on GB300: at 512 threads per
+// block an SM holds two blocks at 48 or at 64 registers alike, and 64 keeps
+// the guard mode's state out of local memory.
 #ifndef TM_WALK_MAXREG
-#define TM_WALK_MAXREG 48
+#define TM_WALK_MAXREG 64
 #endif
 #ifndef TM_WALK_MAXREG_FP64
 #define TM_WALK_MAXREG_FP64 72
@@ -505,7 +524,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
     bool active = false, parked = false, pool_empty = false;
     int32_t m = 0;
     tm_hit *hp = nullptr;
-    const int4 *tet16 = mv0.tet16;
+    const int4 *recs = rec_base<FMT>(mv0);
     const float4 *pts = mv0.pts;
     WalkState<R> S;
     Basis<R> B;
@@ -516,13 +535,14 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
     sc.tau = P.tau_rel * mv0.extent;
     sc.flags = 0;
     uint32_t steps = 0;
+    const int32_t stop = (BOUNDED && !MULTI) ? load_stop(P.stop_tet, mv0.nt) : -1;
 
     for (;;) {
         bool load = false;
         if (MODE == FP32G && parked) {
             // re-decide the step this lane parked, then go on from its new record
             resolve_parked<FMT, BOUNDED>(MULTI ? sdesc[m].mesh : mv0, sc.ray, hp, P.tau_rel,
-                                         P.max_steps, P.stop_tet);
+                                         P.max_steps, stop);
             parked = false;
             load = true;
         }
@@ -540,7 +560,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     const Slot s = find_slot(sdesc, n_meshes, r);
                     m = s.m;
                     local = sdesc[m].perm ? sdesc[m].perm[s.local] : s.local;
-                    tet16 = sdesc[m].mesh.tet16;
+                    recs = rec_base<FMT>(sdesc[m].mesh);
                     pts = sdesc[m].mesh.pts;
                     sc.ray = sdesc[m].rays + local;
                     sc.pts = pts;
@@ -598,7 +618,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
             if (!active) continue;
             // ---- one step of Alg. 6 / Alg. 7 (or Alg. 4-5, Alg. 2-3) ----
             TetRec<FMT> rec;
-            rec.load(mv0, tet16, S.tet);
+            rec.load(mv0, recs, S.tet);
             const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.vx();
             uint32_t code = TM_BOUNDARY;
             bool done = false;
@@ -638,7 +658,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     done = true;
                     code = TM_BOUNDARY;
                     sc.flags |= TM_HIT_STEP_LIMIT;
-                } else if (BOUNDED && next == (uint32_t)P.stop_tet) {
+                } else if (BOUNDED && next == (uint32_t)stop) {
                     // reached the tet that holds the point light (Sec. 6)
                     done = true;
                     code = TM_BOUNDARY;
@@ -703,7 +723,7 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     P.n_cap = W.n_cap;
     P.n_dev = W.n_dev;
     P.tau_rel = W.tau_rel;
-    P.stop_tet = MULTI ? -1 : W.stop_tet;
+    P.stop_tet = MULTI ? nullptr : W.stop_tet;
     const int sms = sm_count_cached();
     int64_t g = (W.n_cap + 255) / 256;
     const int64_t gmax = (int64_t)sms * 16;
@@ -735,8 +755,12 @@ template <bool BOUNDED, bool MULTI>
 cudaError_t dispatch(int mode, int format, const MeshView &mv, const tm_ray *rays, tm_hit *hits,
                      const BatchDesc *descs, int n_meshes, const WalkParams &W, int block, int grid,
                      const cudaEvent_t *ev, cudaStream_t s) {
-    if constexpr (MULTI) {  // batches walk the Tet16 records
-        return dispatch_fmt<TM_FORMAT_TET16, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+    if constexpr (MULTI) {  // batches: formats with one record array per mesh
+        switch (format) {
+            case TM_FORMAT_TET32: return dispatch_fmt<TM_FORMAT_TET32, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            case TM_FORMAT_TET20_AOS: return dispatch_fmt<TM_FORMAT_TET20_AOS, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            default: return dispatch_fmt<TM_FORMAT_TET16, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+        }
     } else {
         switch (format) {
             case TM_FORMAT_TET20: return dispatch_fmt<TM_FORMAT_TET20, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
@@ -772,8 +796,9 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
     for (int i = 0; i < 4; ++i) c.events[i] = o ? (cudaEvent_t)o->phase_events[i] : nullptr;
-    c.format = o ? o->format : TM_FORMAT_TET16;
-    c.stop_tet = -1;
+    c.format = o ? o->format : TM_FORMAT_AUTO;
+    if (c.format == TM_FORMAT_AUTO) c.format = TM_FORMAT_TET32;
+    c.stop_tet = nullptr;
     return c;
 }
 
@@ -835,7 +860,7 @@ tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t t
     W.tau_rel = cfg.tau;
     W.refill = cfg.refill;
     W.batch_steps = cfg.batch_steps;
-    W.stop_tet = -1;
+    W.stop_tet = nullptr;
     int sms = 0;
     int per_sm = max_persistent_ctas(cfg.mode, true, false, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
@@ -844,8 +869,8 @@ tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t t
     if (grid > need) grid = need;
     TM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
     MeshView dummy{};
-    if (cfg.format != TM_FORMAT_TET16) return TM_ERR_ARG;
-    cudaError_t e = dispatch<false, true>(cfg.mode, TM_FORMAT_TET16, dummy, nullptr, nullptr, descs_dev,
+    if (cfg.format == TM_FORMAT_TET20) return TM_ERR_ARG;
+    cudaError_t e = dispatch<false, true>(cfg.mode, cfg.format, dummy, nullptr, nullptr, descs_dev,
                                           n_meshes, W, cfg.block, (int)grid, nullptr, s);
     if (e != cudaSuccess) {
         tm_set_error("trace (batch) launch", e);

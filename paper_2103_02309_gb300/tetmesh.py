@@ -18,8 +18,8 @@ import torch
 from . import _native as N
 
 MODES = {"fp32g": 0, "fp32": 1, "fp64": 2}
-FORMATS = {"tet16": 0, "tet20": 1, "tet32": 2, "tet20_aos": 3}
-ORDERS = {"hilbert": 0, "input": 1}
+FORMATS = {"auto": 0, "tet16": 1, "tet20": 2, "tet32": 3, "tet20_aos": 4}
+ORDERS = {"hilbert": 0, "input": 1, "hilbert_regions": 2}
 
 HIT_SIDE_NEG = 0x01
 HIT_STEP_LIMIT = 0x02
@@ -58,7 +58,7 @@ def _hptr(a: np.ndarray):
 
 
 def trace_opts(mode="fp32g", guard_tau=0.0, max_steps=0, block=0, refill=0, batch_steps=0,
-               ctas_per_sm=0, tmax_early_exit=False, phase_events=None, format="tet16") -> N.TraceOpts:
+               ctas_per_sm=0, tmax_early_exit=False, phase_events=None, format="auto") -> N.TraceOpts:
     """Trace options; phase_events: four torch.cuda.Event (enable_timing) recorded
     before the start phase, after it, after the walk and after the finish phase."""
     o = N.TraceOpts()
@@ -202,15 +202,16 @@ class Mesh:
                                ctypes.byref(o), _stream(stream)), "tm_trace")
         return hits
 
-    def trace_shadow(self, rays: torch.Tensor, light_tet: int, hits: torch.Tensor | None = None,
-                     n_dev: torch.Tensor | None = None, opts: N.TraceOpts | None = None,
-                     stream=None, **kw) -> torch.Tensor:
-        """Walks that also end (flag HIT_REACHED) on entering the light's tet."""
+    def trace_shadow(self, rays: torch.Tensor, light_tet: torch.Tensor,
+                     hits: torch.Tensor | None = None, n_dev: torch.Tensor | None = None,
+                     opts: N.TraceOpts | None = None, stream=None, **kw) -> torch.Tensor:
+        """Walks that also end (flag HIT_REACHED) on entering the light's tet
+        (light_tet: device int32 tensor, e.g. from locate)."""
         n = rays.shape[0]
         if hits is None:
             hits = torch.empty((n, 8), dtype=torch.int32, device=rays.device)
         o = opts if opts is not None else trace_opts(**kw)
-        N.check(N.lib.tm_trace_shadow(self._h, _dptr(rays), n, _dptr(n_dev), int(light_tet),
+        N.check(N.lib.tm_trace_shadow(self._h, _dptr(rays), n, _dptr(n_dev), _dptr(light_tet),
                                       _dptr(hits), ctypes.byref(o), _stream(stream)),
                 "tm_trace_shadow")
         return hits

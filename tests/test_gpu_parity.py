@@ -246,10 +246,12 @@ def test_record_formats_identical(tmx, mode):
             compare(scene.points, scene.tris, got["tet32"], w, check_t=(mode != "fp32"))
 
 
-def test_hilbert_and_input_order_identical(tmx):
+@pytest.mark.parametrize("other", ["input", "hilbert_regions"])
+def test_hilbert_and_other_orders_identical(tmx, other):
+    """Reordering (Sec. 5) changes where records live, not the walk: identical hits."""
     s = sg.make_config("medium", n_override=32)
     a = Case(tmx, s, "hilbert")
-    b = Case(tmx, s, "input")
+    b = Case(tmx, s, other)
     eye = np.array([s.camera.eye], np.float32)
     cin, _ = a.om.locate(eye)
     o, d = sg.camera_rays(sg.Camera(s.camera.eye, 70.0, 320, 180))

@@ -90,7 +90,7 @@ def test_shadow_trace_matches_oracle(tmx, request, scene, mode):
                                         np.float32(w["b2"]), L)
     _, lt = light_tet(c, L)
     rays = dev(tmx.pack_rays(o2, d2, tm2, -1 - entry))
-    g = tmx.unpack_hits(c.mesh.trace_shadow(rays, lt, mode=mode))
+    g = tmx.unpack_hits(c.mesh.trace_shadow(rays, dev(np.array([lt], np.int32)), mode=mode))
     wo = c.oracle_trace(o2, d2, tm2, -1, entry)
     st = compare(c.s.points, c.s.tris, g, wo, check_t=(mode != "fp32"))
     reached = (g["flags"] & tmx.HIT_REACHED) != 0
@@ -111,7 +111,7 @@ def test_shadow_ray_from_inside_the_light_tet(tmx, tiny):
     d = np.array([[0.3, -0.2, 0.9]], np.float32)
     d /= np.linalg.norm(d)
     rays = dev(tmx.pack_rays(q, d, 1e-3, np.array([lt], np.int32)))
-    g = tmx.unpack_hits(c.mesh.trace_shadow(rays, lt))
+    g = tmx.unpack_hits(c.mesh.trace_shadow(rays, dev(np.array([lt], np.int32))))
     assert g["tri"][0] == -1 and g["flags"][0] & tmx.HIT_REACHED and g["steps"][0] == 0
 
 

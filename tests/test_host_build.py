@@ -176,3 +176,36 @@ def test_tet20_records(tmx):
     from paper_2103_02309_gb300 import _native as N
     with pytest.raises(N.TetmeshError):
         tmx.Mesh(s.points, s.tets, s.tris, upload=False).export_tet20()
+
+
+def test_hilbert_regions_order(tmx):
+    """Regions (Sec. 5): tets enclosed by the same constrained faces are stored
+    together, regions in order of their first Hilbert key, Hilbert order inside.
+
+    Reference regions come from the scene's cell labels: on the Kuhn grid two
+    cells share a non-constrained face exactly when both are inside or both
+    outside, so the regions are the face-connected components of the inside
+    cells and of the outside cells."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    n = 16
+    s = sg.make_config("medium", n_override=n)
+    m = tmx.Mesh(s.points, s.tets, s.tris, order="hilbert_regions", upload=False)
+    e = m.export()
+    lab_in, k_in = ndimage.label(s.inside)
+    lab_out, k_out = ndimage.label(~s.inside)
+    cell_region = np.where(s.inside, lab_in - 1, k_in + lab_out - 1).ravel()  # [k, j, i] order
+    tet_region = np.repeat(cell_region, 6)                                   # tet = 6*cube + p
+    assert m.info.n_regions == k_in + k_out
+    internal_region = tet_region[e["tet_perm"]]
+    # each region occupies one contiguous run of internal ids
+    changes = np.count_nonzero(np.diff(internal_region)) + 1
+    assert changes == k_in + k_out
+    # Hilbert keys of the centroids (2^21 grid over the unit cube) rise inside a region,
+    # and regions follow the order of their smallest key
+    c = s.points.astype(np.float64)[s.tets].mean(axis=1)[e["tet_perm"]]
+    q = np.clip(np.floor(c * 2097152.0), 0, 2097151).astype(np.uint32)
+    key = tmx.hilbert_keys(q, 21)
+    same = internal_region[1:] == internal_region[:-1]
+    assert (key[1:][same] >= key[:-1][same]).all()
+    starts = np.concatenate([[0], np.nonzero(~same)[0] + 1])
+    assert (np.diff(key[starts].astype(np.float64)) > 0).all()
