@@ -16,7 +16,10 @@
 //    broken by vertex ids (the pair decides as if id_a < id_b gave +), so a
 //    pair of vertices gets the same answer in every tet of a ray's walk.
 //    In guard mode a test with |det| < tau * max|coordinate| is re-decided
-//    from double-precision projections of the two float32 points.
+//    in double precision from the 3-D points: with A = a - o and B = b - o,
+//    det(P(a), P(b)) = (u.A)(v.B) - (v.A)(u.B) = (A x B).(u x v) (Binet-
+//    Cauchy), and u x v = (|u|^2 / |t_min|) d points along d, so the sign is
+//    that of the triple product (A x B).d: no basis, no division.
 //  * Exit face (Alg. 1): with the entry face p0, p1, p2 counter-clockwise
 //    around the origin, the new vertex p3 replaces slot e, and the kept
 //    face is again counter-clockwise (Sec. 4: "the counterclockwise
@@ -110,6 +113,16 @@ __device__ __forceinline__ Basis<R> make_basis(R dx, R dy, R dz, R ox, R oy, R o
     return b;
 }
 
+// ((a - o) x (b - o)) . d in double precision from the float32 inputs: a
+// positive multiple of det(P(a), P(b)) in the ray's basis (see the header).
+__device__ __forceinline__ double triple(const float4 &o, const float4 &d, const float4 &a,
+                                         const float4 &b) {
+    const double ax = (double)a.x - o.x, ay = (double)a.y - o.y, az = (double)a.z - o.z;
+    const double bx = (double)b.x - o.x, by = (double)b.y - o.y, bz = (double)b.z - o.z;
+    const double cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+    return cx * d.x + cy * d.y + cz * d.z;
+}
+
 // Double-precision sign decision of det(p_a, p_b) for two float32 points of
 // one ray (the guard's re-test).  Out of line by default: it is the rare path.
 #ifdef TM_GUARD_INLINE
@@ -121,10 +134,7 @@ __device__ TM_GUARD_ATTR static double guard_det(const tm_ray *ray, const float4
                                                 int32_t ib) {
     const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
     const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
-    const Basis<double> B = make_basis<double>(w1.x, w1.y, w1.z, w0.x, w0.y, w0.z);
-    const float4 a = __ldg(pts + ia), b = __ldg(pts + ib);
-    const P2<double> pa = B.project(a.x, a.y, a.z), pb = B.project(b.x, b.y, b.z);
-    return det2(pa, pb);
+    return triple(w0, w1, __ldg(pts + ia), __ldg(pts + ib));
 }
 
 // tau * max(|p.x|, |p.y|): the guard threshold contribution of one point.
@@ -279,8 +289,8 @@ __device__ __noinline__ static int2 step3d(const MeshView &mv, const tm_ray *ray
 }
 
 // Guard mode: the three sign tests of one step when at least one of them is
-// within its threshold (or exactly zero), re-decided from double-precision
-// projections of the two points (ties broken by vertex ids).  Out of line:
+// within its threshold (or exactly zero), re-decided by the double-precision
+// triple product of the two points (ties broken by vertex ids).  Out of line:
 // the rare path.  Returns the three signs in bits 0..2 and TM_HIT_GUARD /
 // TM_HIT_TIE in bits 8 and up.
 __device__ __forceinline__ uint32_t guard_signs_impl(const tm_ray *ray, const float4 *pts, float d0,
@@ -288,9 +298,7 @@ __device__ __forceinline__ uint32_t guard_signs_impl(const tm_ray *ray, const fl
                                                      int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
     const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
     const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
-    const Basis<double> B = make_basis<double>(w1.x, w1.y, w1.z, w0.x, w0.y, w0.z);
     const float4 x3 = __ldg(pts + i3);
-    const P2<double> q3 = B.project(x3.x, x3.y, x3.z);
     const float d[3] = {d0, d1, d2}, t[3] = {t0, t1, t2};
     const int32_t id[3] = {i0, i1, i2};
     uint32_t bits = 0, flags = 0;
@@ -300,8 +308,7 @@ __device__ __forceinline__ uint32_t guard_signs_impl(const tm_ray *ray, const fl
             pos = d[k] > 0.f;
         } else {
             flags |= TM_HIT_GUARD;
-            const float4 x = __ldg(pts + id[k]);
-            const double dd = det2(q3, B.project(x.x, x.y, x.z));
+            const double dd = triple(w0, w1, x3, __ldg(pts + id[k]));
             if (dd != 0.0) {
                 pos = dd > 0.0;
             } else {
