@@ -52,7 +52,8 @@ RAY_BYTES, HIT_BYTES = 32, 32
 # point; per ray its start record (32 B, in the hit slot), the ray (32 B),
 # the three entry-face points (48 B) and the end record (32 B).
 WALK_RAY_BYTES = 32 + RAY_BYTES + 3 * 16 + 32
-RECORD_BYTES = {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32}
+RECORD_BYTES = {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32, "face": 32}
+POINT_BYTES = {"face": 0}   # face entries carry the new vertex; the others read a float4 point
 # Rays generated from each hit: (rays per hit, tmax); None = per-ray (shadow)
 SECONDARY = {"bounce": (1, float("inf")), "ao": (8, 0.05), "shadow": (1, None),
              "reflect": (1, float("inf")), "refract": (1, float("inf"))}
@@ -85,8 +86,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="precision")
     p.add_argument("--order", choices=["hilbert", "input", "hilbert_regions"], default="hilbert")
-    p.add_argument("--format", choices=sorted(RECORD_BYTES), default="tet32",
-                   help="tet record the walk reads (tet32 is the library's automatic choice)")
+    p.add_argument("--format", choices=sorted(RECORD_BYTES), default="face",
+                   help="tet record the walk reads (face entries: the library's automatic choice "
+                        "when the mesh has them)")
     p.add_argument("--secondary", choices=sorted(SECONDARY), default=None,
                    help="rays generated from the primary hits (default: the workload's)")
     p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
@@ -227,12 +229,12 @@ def run_ours(args, world, rank, local):
     s = build_scene(args.workload)
     t0 = time.time()
     mesh = tmx.Mesh(s.points, s.tets, s.tris, order=args.order,
-                    tet20=args.format.startswith("tet20"))
+                    tet20=args.format.startswith("tet20"), faces=args.format == "face")
     build_s = time.time() - t0
     cam = tmx.make_camera(s.camera.eye, s.camera.fov_deg, s.camera.width, s.camera.height)
     n_primary = s.camera.width * s.camera.height
     per_hit = W["per_hit"]
-    default_run = (kind == WORKLOADS[args.workload]["kind"] and args.format == "tet32"
+    default_run = (kind == WORKLOADS[args.workload]["kind"] and args.format == "face"
                    and args.order == "hilbert")
     dev = torch.device("cuda", local)
     eye = torch.tensor([s.camera.eye], dtype=torch.float32, device=dev)
@@ -310,7 +312,7 @@ def run_ours(args, world, rank, local):
     g1 = tmx.unpack_hits(hits)
     g2 = tmx.unpack_hits(hits2[:n_second])
     steps_total = int(g1["steps"].astype(np.int64).sum() + g2["steps"].astype(np.int64).sum())
-    step_bytes = RECORD_BYTES[args.format] + 16
+    step_bytes = RECORD_BYTES[args.format] + POINT_BYTES.get(args.format, 16)
     alg_bytes = steps_total * step_bytes + rays_per_step * WALK_RAY_BYTES
     guard_rate = float(((g1["flags"] & tmx.HIT_GUARD) != 0).mean())
     fl = np.concatenate([g1["flags"], g2["flags"]])
@@ -539,7 +541,7 @@ def run_batched(args, world, rank, local):
     for dsc in descs:
         s = sg.make_grid_scene("batched", dsc["n"], sg.BATCHED["jitter"], dsc["seed"],
                                n_spheres=dsc["n_spheres"])
-        mesh = tmx.Mesh(s.points, s.tets, s.tris)
+        mesh = tmx.Mesh(s.points, s.tets, s.tris, faces=True)
         n_prim = dsc["primary"]
         side = max(1, int(math.ceil(math.sqrt(n_prim))))
         cam = tmx.make_camera(sg.BATCHED["camera_eye"], sg.BATCHED["fov_deg"], side,

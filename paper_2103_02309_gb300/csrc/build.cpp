@@ -182,6 +182,7 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
     const int order = opts ? opts->order : TM_ORDER_HILBERT;
     const bool fix = opts ? opts->fix_orientation != 0 : false;
     const bool want_t20 = opts ? opts->tet20 != 0 : false;
+    const bool want_face = opts ? opts->faces != 0 : false;
     if (order != TM_ORDER_HILBERT && order != TM_ORDER_INPUT && order != TM_ORDER_HILBERT_REGIONS)
         return TM_ERR_ARG;
     m->np = np;
@@ -422,6 +423,32 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
             m->t20aos[5 * tn + 4] = (int32_t)n3;
         }
     }
+    if (want_face) {
+        // face entry r of tet T: the face opposite T's vertex of rank r; the
+        // neighbour N across it and N's vertex opposite the shared face
+        m->face.assign((size_t)nt * 32, 0);
+#pragma omp parallel for schedule(static)
+        for (int64_t tn = 0; tn < nt; ++tn) {
+            const int32_t *V = &m->cold[8 * tn];
+            const int32_t *NB = &m->cold[8 * tn + 4];
+            int idx[4] = {0, 1, 2, 3};
+            std::sort(idx, idx + 4, [&](int x, int y) { return V[x] < V[y]; });
+            for (int r = 0; r < 4; ++r) {
+                int32_t *e = &m->face[32 * tn + 8 * r];
+                const uint32_t nb = (uint32_t)NB[idx[r]];
+                e[0] = (int32_t)nb;
+                e[1] = -1;
+                if (nb & TM_CFACE_FLAG) continue;
+                const int32_t *V2 = &m->cold[8 * (int64_t)nb];
+                const int32_t *N2 = &m->cold[8 * (int64_t)nb + 4];
+                for (int j = 0; j < 4; ++j)
+                    if (N2[j] == (int32_t)tn) {
+                        e[1] = V2[j];
+                        std::memcpy(&e[2], &m->pts4[4 * (int64_t)V2[j]], 3 * sizeof(float));
+                    }
+            }
+        }
+    }
     m->cface.resize((size_t)nc * 8);
 #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c) {
@@ -493,6 +520,11 @@ tm_status tm_upload(tm_mesh *m) {
                            cudaMemcpyHostToDevice));
         m->device_bytes += (int64_t)(40 * m->nt);
     }
+    if (!m->face.empty()) {
+        TM_CUDA(cudaMalloc(&m->d_face, 128 * (size_t)m->nt));
+        TM_CUDA(cudaMemcpy(m->d_face, m->face.data(), 128 * (size_t)m->nt, cudaMemcpyHostToDevice));
+        m->device_bytes += (int64_t)(128 * m->nt);
+    }
     m->on_device = true;
     // seed lattice: locate the centres of a kSeedGrid^3 lattice over the
     // bounding cube once, from the default source tet
@@ -540,6 +572,8 @@ void tm_free_device(tm_mesh *m) {
     cudaFree(m->d_t20);
     cudaFree(m->d_t20n3);
     cudaFree(m->d_t20aos);
+    cudaFree(m->d_face);
+    m->d_face = nullptr;
     m->d_t20 = nullptr;
     m->d_t20n3 = nullptr;
     m->d_t20aos = nullptr;

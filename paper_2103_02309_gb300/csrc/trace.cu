@@ -314,6 +314,8 @@ finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ r
 template <class R, bool BOUNDED> struct Depth {
     __device__ __forceinline__ void init(const float4 &, const float4 &) {}
     __device__ __forceinline__ void set(int, const float4 &) {}
+    __device__ __forceinline__ R depth(const float4 &) const { return R(0); }
+    __device__ __forceinline__ void put(int, R) {}
     __device__ __forceinline__ bool beyond() const { return false; }
 };
 template <class R> struct Depth<R, true> {
@@ -326,10 +328,10 @@ template <class R> struct Depth<R, true> {
     __device__ __forceinline__ R depth(const float4 &p) const {
         return rfma(dz, R(p.z), rfma(dy, R(p.y), rmul(dx, R(p.x)))) - dod;
     }
-    __device__ __forceinline__ void set(int slot, const float4 &p) {
-        const R z = depth(p);
+    __device__ __forceinline__ void put(int slot, R z) {
         if (slot == 0) z0 = z; else if (slot == 1) z1 = z; else z2 = z;
     }
+    __device__ __forceinline__ void set(int slot, const float4 &p) { put(slot, depth(p)); }
     // the entry face of the next tet lies entirely beyond t_max
     __device__ __forceinline__ bool beyond() const { return fmin(z0, fmin(z1, z2)) > zmax; }
 };
@@ -342,7 +344,8 @@ template <class R> struct Depth<R, true> {
 template <int FMT> struct TetRec;
 
 template <int FMT> __device__ __forceinline__ const int4 *rec_base(const MeshView &mv) {
-    return FMT == TM_FORMAT_TET32 ? mv.cold
+    return FMT == TM_FORMAT_FACE ? mv.face
+         : FMT == TM_FORMAT_TET32 ? mv.cold
          : FMT == TM_FORMAT_TET20 ? mv.t20
          : FMT == TM_FORMAT_TET20_AOS ? reinterpret_cast<const int4 *>(mv.t20aos)
                                       : mv.tet16;
@@ -397,11 +400,29 @@ template <> struct TetRec<TM_FORMAT_TET20_AOS> {  // the same, packed at a 20-by
     }
 };
 
+// One 32-byte record in a single 256-bit load (sm_100 and later; the cold
+// records are 32-byte aligned), or as two 128-bit loads.
+#ifndef TM_LD256
+#define TM_LD256 1
+#endif
+__device__ __forceinline__ void load32(const int4 *p, int4 &a, int4 &b) {
+#if TM_LD256
+    // four 64-bit lanes (the eight-word form of the same load stops this
+    // toolchain's compiler on this kernel)
+    unsigned long long q0, q1, q2, q3;
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3) : "l"(p));
+    a = make_int4((int)(uint32_t)q0, (int)(q0 >> 32), (int)(uint32_t)q1, (int)(q1 >> 32));
+    b = make_int4((int)(uint32_t)q2, (int)(q2 >> 32), (int)(uint32_t)q3, (int)(q3 >> 32));
+#else
+    a = __ldg(p);
+    b = __ldg(p + 1);
+#endif
+}
+
 template <> struct TetRec<TM_FORMAT_TET32> {  // V_0..V_3 and N_j across V_j (the cold record)
     int4 v, nb;
     __device__ __forceinline__ void load(const MeshView &, const int4 *base, int32_t t) {
-        v = __ldg(base + 2 * t);
-        nb = __ldg(base + 2 * t + 1);
+        load32(base + 2 * (int64_t)t, v, nb);
     }
     __device__ __forceinline__ int32_t vx() const { return v.x ^ v.y ^ v.z ^ v.w; }
     __device__ __forceinline__ uint32_t next(int32_t, int32_t, int32_t, int32_t, int32_t,
@@ -454,8 +475,10 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
     S.m0 = guard_mag(S.p0, sc.tau);
     S.m1 = guard_mag(S.p1, sc.tau);
     S.m2 = guard_mag(S.p2, sc.tau);
-    TetRec<FMT> rec;
-    rec.load(mv, rec_base<FMT>(mv), S.tet);
+    // the face-entry walk re-decides from the full record (same neighbours)
+    constexpr int RF = FMT == TM_FORMAT_FACE ? TM_FORMAT_TET32 : FMT;
+    TetRec<RF> rec;
+    rec.load(mv, rec_base<RF>(mv), S.tet);
     const int32_t i3 = S.i0 ^ S.i1 ^ S.i2 ^ rec.vx();
     if ((uint32_t)i3 >= (uint32_t)mv.np) {
         put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
@@ -536,6 +559,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
     sc.flags = 0;
     uint32_t steps = 0;
     const int32_t stop = (BOUNDED && !MULTI) ? load_stop(P.stop_tet, mv0.nt) : -1;
+    R z3 = R(0);  // face entries, bounded walks: depth of the current tet's fourth vertex
 
     for (;;) {
         bool load = false;
@@ -608,6 +632,21 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                         active = false;
                     }
                 }
+                if (FMT == TM_FORMAT_FACE && active) {
+                    // the fourth vertex of the tet entered, from its full record
+                    int4 cv, cn;
+                    load32((MULTI ? sdesc[m].mesh.cold : mv0.cold) + 2 * (int64_t)S.tet, cv, cn);
+                    S.i3 = cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2;
+                    if ((uint32_t)S.i3 >= (uint32_t)(MULTI ? sdesc[m].mesh.np : mv0.np)) {
+                        put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
+                        active = false;
+                    } else {
+                        const float4 x3 = __ldg(pts + S.i3);
+                        S.p3 = B.project(R(x3.x), R(x3.y), R(x3.z));
+                        if (MODE == FP32G) S.m3 = guard_mag(S.p3, sc.tau);
+                        if (BOUNDED) z3 = Z.depth(x3);
+                    }
+                }
             }
         }
         if (!__any_sync(kFull, active || parked)) {
@@ -616,6 +655,62 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
         }
         for (int k = 0; k < P.batch_steps; ++k) {
             if (!active) continue;
+            if constexpr (FMT == TM_FORMAT_FACE) {
+                // ---- one step over face entries: Alg. 1 on the vertex known
+                // since entering the tet, then one 32-byte read ----
+                const uint32_t sig = step_signs<MODE, MODE == FP32G, false>(S, S.p3, S.i3, S.m3, sc);
+                if (MODE == FP32G && sig == kParked) {
+                    put_record(hp, 2, S.tet, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
+                    active = false;
+                    parked = true;
+                    continue;
+                }
+                const int e = exit_slot_bits(sig);
+                const int32_t ie = e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2);
+                const int rb = (S.i0 < ie) + (S.i1 < ie) + (S.i2 < ie) + (S.i3 < ie);
+                int4 fa, fb;
+                load32(recs + 2 * (4 * (int64_t)S.tet + rb), fa, fb);
+                if (e == 0) { S.i0 = S.i3; S.p0 = S.p3; S.m0 = S.m3; }
+                else if (e == 1) { S.i1 = S.i3; S.p1 = S.p3; S.m1 = S.m3; }
+                else { S.i2 = S.i3; S.p2 = S.p3; S.m2 = S.m3; }
+                if (BOUNDED) Z.put(e, z3);
+                ++steps;
+                const uint32_t next = (uint32_t)fa.x;
+                uint32_t code = next;
+                bool done = false;
+                if (next & TM_CFACE_FLAG) {
+                    done = true;
+                } else if (next >= (uint32_t)(MULTI ? sdesc[m].mesh.nt : mv0.nt)) {
+                    done = true;
+                    code = TM_BOUNDARY;
+                    sc.flags |= TM_HIT_BAD_ID;
+                } else if (steps >= P.max_steps) {
+                    done = true;
+                    code = TM_BOUNDARY;
+                    sc.flags |= TM_HIT_STEP_LIMIT;
+                } else if (BOUNDED && next == (uint32_t)stop) {
+                    done = true;
+                    code = TM_BOUNDARY;
+                    sc.flags |= TM_HIT_REACHED;
+                    S.tet = (int32_t)next;
+                } else if (BOUNDED && Z.beyond()) {
+                    done = true;
+                    code = TM_BOUNDARY;
+                } else {
+                    S.prev = S.tet;
+                    S.tet = (int32_t)next;
+                    S.i3 = fa.y;
+                    const float4 x3 = make_float4(__int_as_float(fa.z), __int_as_float(fa.w),
+                                                  __int_as_float(fb.x), 0.f);
+                    S.p3 = B.project(R(x3.x), R(x3.y), R(x3.z));
+                    if (MODE == FP32G) S.m3 = guard_mag(S.p3, sc.tau);
+                    if (BOUNDED) z3 = Z.depth(x3);
+                }
+                if (done) {
+                    put_end(hp, S.tet, code, steps, sc.flags);
+                    active = false;
+                }
+            } else {
             // ---- one step of Alg. 6 / Alg. 7 (or Alg. 4-5, Alg. 2-3) ----
             TetRec<FMT> rec;
             rec.load(mv0, recs, S.tet);
@@ -676,6 +771,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 put_end(hp, S.tet, code, steps, sc.flags);
                 active = false;
             }
+            }  // record formats
         }
     }
 }
@@ -759,6 +855,7 @@ cudaError_t dispatch(int mode, int format, const MeshView &mv, const tm_ray *ray
         switch (format) {
             case TM_FORMAT_TET32: return dispatch_fmt<TM_FORMAT_TET32, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
             case TM_FORMAT_TET20_AOS: return dispatch_fmt<TM_FORMAT_TET20_AOS, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            case TM_FORMAT_FACE: return dispatch_fmt<TM_FORMAT_FACE, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
             default: return dispatch_fmt<TM_FORMAT_TET16, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
         }
     } else {
@@ -766,6 +863,7 @@ cudaError_t dispatch(int mode, int format, const MeshView &mv, const tm_ray *ray
             case TM_FORMAT_TET20: return dispatch_fmt<TM_FORMAT_TET20, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
             case TM_FORMAT_TET32: return dispatch_fmt<TM_FORMAT_TET32, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
             case TM_FORMAT_TET20_AOS: return dispatch_fmt<TM_FORMAT_TET20_AOS, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
+            case TM_FORMAT_FACE: return dispatch_fmt<TM_FORMAT_FACE, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
             default: return dispatch_fmt<TM_FORMAT_TET16, BOUNDED, MULTI>(mode, mv, rays, hits, descs, n_meshes, W, block, grid, ev, s);
         }
     }
@@ -796,8 +894,7 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
     for (int i = 0; i < 4; ++i) c.events[i] = o ? (cudaEvent_t)o->phase_events[i] : nullptr;
-    c.format = o ? o->format : TM_FORMAT_AUTO;
-    if (c.format == TM_FORMAT_AUTO) c.format = TM_FORMAT_TET32;
+    c.format = o ? o->format : TM_FORMAT_AUTO;  // resolved against the mesh at launch
     c.stop_tet = nullptr;
     return c;
 }
@@ -805,14 +902,18 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
 static bool valid_config(const TraceConfig &c) {
     return (c.mode == FP32G || c.mode == FP32 || c.mode == FP64) &&
            (c.format == TM_FORMAT_TET16 || c.format == TM_FORMAT_TET20 || c.format == TM_FORMAT_TET32 ||
-            c.format == TM_FORMAT_TET20_AOS) &&
+            c.format == TM_FORMAT_TET20_AOS || c.format == TM_FORMAT_FACE) &&
            c.block >= 32 &&
            c.block <= 1024 && c.block % 32 == 0 && c.refill >= 1 && c.refill <= 32 &&
            c.batch_steps >= 1 && c.batch_steps <= 256 && c.ctas_per_sm >= 0;
 }
 
+int auto_format(bool has_faces) { return has_faces ? TM_FORMAT_FACE : TM_FORMAT_TET32; }
+
 tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const int64_t *n_dev,
-                       tm_hit *hits, const TraceConfig &cfg, cudaStream_t s) {
+                       tm_hit *hits, const TraceConfig &cfg_in, cudaStream_t s) {
+    TraceConfig cfg = cfg_in;
+    if (cfg.format == TM_FORMAT_AUTO) cfg.format = auto_format(mv.face != nullptr);
     if (!valid_config(cfg)) return TM_ERR_ARG;
     if (n == 0) return TM_OK;
     if (n > INT32_MAX) return TM_ERR_TOO_LARGE;

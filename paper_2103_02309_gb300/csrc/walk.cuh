@@ -189,6 +189,10 @@ template <class R> struct WalkState {
     int32_t i0, i1, i2;
     P2<R> p0, p1, p2;
     float m0, m1, m2;  // guard mode: tau * max(|p.x|, |p.y|) of each slot
+    // face-entry walk: the current tet's fourth vertex, known on entering it
+    int32_t i3;
+    P2<R> p3;
+    float m3;
 };
 
 

@@ -18,7 +18,7 @@ import torch
 from . import _native as N
 
 MODES = {"fp32g": 0, "fp32": 1, "fp64": 2}
-FORMATS = {"auto": 0, "tet16": 1, "tet20": 2, "tet32": 3, "tet20_aos": 4}
+FORMATS = {"auto": 0, "tet16": 1, "tet20": 2, "tet32": 3, "tet20_aos": 4, "face": 5}
 ORDERS = {"hilbert": 0, "input": 1, "hilbert_regions": 2}
 
 HIT_SIDE_NEG = 0x01
@@ -122,11 +122,12 @@ class Mesh:
     """A compact constrained tet mesh on the current CUDA device."""
 
     def __init__(self, points, tets, tris, order="hilbert", upload=True, fix_orientation=False,
-                 tet20=False):
+                 tet20=False, faces=False):
         pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
         tt = np.ascontiguousarray(tets, np.int32).reshape(-1, 4)
         tr = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
-        o = N.BuildOpts(ORDERS[order], 1 if fix_orientation else 0, 1 if tet20 else 0)
+        o = N.BuildOpts(ORDERS[order], 1 if fix_orientation else 0, 1 if tet20 else 0,
+                        1 if faces else 0)
         h = ctypes.c_void_p()
         N.check(N.lib.tm_build(_hptr(pts), len(pts), _hptr(tt), len(tt),
                                _hptr(tr) if len(tr) else None, len(tr), ctypes.byref(o),
@@ -173,6 +174,12 @@ class Mesh:
         N.check(N.lib.tm_mesh_export_tet20(self._h, _hptr(vxn), _hptr(n3), _hptr(aos)),
                 "tm_mesh_export_tet20")
         return dict(vxn=vxn, n3=n3, aos=aos)
+
+    def export_faces(self) -> np.ndarray:
+        """Face entries int32 [n_tets, 4, 8] (see TM_FORMAT_FACE)."""
+        f = np.empty((self.n_tets, 4, 8), np.int32)
+        N.check(N.lib.tm_mesh_export_faces(self._h, _hptr(f)), "tm_mesh_export_faces")
+        return f
 
     def map_ids(self, kind, direction, ids) -> np.ndarray:
         a = np.ascontiguousarray(ids, np.int32).reshape(-1)

@@ -29,10 +29,10 @@ def dev(a):
 
 
 class Case:
-    def __init__(self, tmx, scene, order="hilbert"):
+    def __init__(self, tmx, scene, order="hilbert", faces=False):
         self.s = scene
         self.om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
-        self.mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, order=order)
+        self.mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, order=order, faces=faces)
         e = self.mesh.export()
         self.tperm = e["tet_perm"]
         self.tinv = np.empty_like(self.tperm)
@@ -82,11 +82,11 @@ def tiny(tmx):
     return camera_case(tmx, "tiny")
 
 
-def random_case(tmx, n, seed, frac=0.3, jitter=0.2):
+def random_case(tmx, n, seed, frac=0.3, jitter=0.2, faces=False):
     pts, tets = sg.freudenthal_grid(n, jitter, seed)
     inside = np.random.default_rng(seed).random((n, n, n)) < frac
     tris = sg.constrained_faces(n, inside)
-    return Case(tmx, sg.Scene("random", n, jitter, seed, pts, tets, tris, inside))
+    return Case(tmx, sg.Scene("random", n, jitter, seed, pts, tets, tris, inside), faces=faces)
 
 
 def random_rays(case, count, seed):
@@ -219,13 +219,13 @@ def test_gen_secondary_matches_generator(tmx, tiny):
 
 @pytest.mark.parametrize("mode", ["fp32g", "fp32", "fp64"])
 def test_record_formats_identical(tmx, mode):
-    """Tet16, Tet20 (split and packed) and Tet32 walks (Alg. 7, 5, 3) take the same steps: identical hits."""
+    """Tet16, Tet20 (split and packed), Tet32 and face-entry walks (Alg. 7, 5, 3) take the same steps: identical hits."""
     for scene in (sg.make_config("tiny"), None):
         if scene is None:
             c0 = random_case(tmx, 6, 515)
             scene = c0.s
         om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
-        mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, tet20=True)
+        mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, tet20=True, faces=True)
         tinv = np.empty(scene.n_tets, np.int64)
         tinv[mesh.export()["tet_perm"]] = np.arange(scene.n_tets)
         g = np.random.default_rng(8)
@@ -238,8 +238,8 @@ def test_record_formats_identical(tmx, mode):
             rays = dev(tmx.pack_rays(q[keep], d[keep], tmax, tinv[start[keep]]))
             got = {f: tmx.unpack_hits(mesh.trace(rays, mode=mode, format=f,
                                                  tmax_early_exit=np.isfinite(tmax)))
-                   for f in ("tet16", "tet20", "tet20_aos", "tet32")}
-            for f in ("tet20", "tet20_aos", "tet32"):
+                   for f in ("tet16", "tet20", "tet20_aos", "tet32", "face")}
+            for f in ("tet20", "tet20_aos", "tet32", "face"):
                 for k in ("tri", "t", "b1", "b2", "tet", "steps", "flags"):
                     assert np.array_equal(got[f][k], got["tet16"][k]), (f, k)
             w = om.trace(q[keep], d[keep], tmax, start[keep])
@@ -310,8 +310,12 @@ def test_precision_full_size_sampled(tmx, precision, mode):
     print(mode, "primary", st, "bounce", st2)
 
 
-def test_batch_matches_single_launches(tmx):
-    cases = [random_case(tmx, n, 300 + n) for n in (3, 5, 6, 4)]
+@pytest.mark.parametrize("faces", [False, True])
+def test_batch_matches_single_launches(tmx, faces):
+    """One persistent launch over uneven meshes equals one launch per mesh, for
+    every record format a batch can walk (the default picks face entries when
+    every mesh has them)."""
+    cases = [random_case(tmx, n, 300 + n, faces=faces) for n in (3, 5, 6, 4)]
     counts = [2500, 0, 1, 7777]
     rays, want, data = [], [], []
     for c, cnt in zip(cases, counts):
@@ -326,19 +330,22 @@ def test_batch_matches_single_launches(tmx):
         data.append((o, d, st))
     b = tmx.Batch([c.mesh for c in cases])
     hits = [torch.empty((r.shape[0], 8), dtype=torch.int32, device="cuda") for r in rays]
-    for chunk in (0, 256):
-        for h in hits:
-            h.fill_(-7)
-        b.set(rays, hits, sort_chunk=chunk)
-        b.run()
-        torch.cuda.synchronize()
-        for c, h, wnt, (o, d, st) in zip(cases, hits, want, data):
-            if wnt is None:
-                continue
-            got = tmx.unpack_hits(h)
-            for k in ("tri", "t", "b1", "b2", "tet", "steps"):
-                assert np.array_equal(got[k], wnt[k]), (chunk, k)
-            compare(c.s.points, c.s.tris, got, c.oracle_trace(o, d, np.inf, st))
+    formats = ["auto", "tet16", "tet32"] + (["face"] if faces else [])
+    for fmt in formats:
+        for chunk in (0, 256):
+            for h in hits:
+                h.fill_(-7)
+            b.set(rays, hits, sort_chunk=chunk, format=fmt)
+            b.run()
+            torch.cuda.synchronize()
+            for c, h, wnt, (o, d, st) in zip(cases, hits, want, data):
+                if wnt is None:
+                    continue
+                got = tmx.unpack_hits(h)
+                for k in ("tri", "t", "b1", "b2", "tet", "steps"):
+                    assert np.array_equal(got[k], wnt[k]), (fmt, chunk, k)
+                compare(c.s.points, c.s.tris, got, c.oracle_trace(o, d, np.inf, st))
+    b.set(rays, hits)
     for h in hits:
         h.fill_(-7)
     b.run_separate()

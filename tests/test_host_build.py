@@ -209,3 +209,30 @@ def test_hilbert_regions_order(tmx):
     assert (key[1:][same] >= key[:-1][same]).all()
     starts = np.concatenate([[0], np.nonzero(~same)[0] + 1])
     assert (np.diff(key[starts].astype(np.float64)) > 0).all()
+
+
+def test_face_entries(tmx):
+    """Face entries: entry r of tet T is the face opposite T's vertex of rank r,
+    holding the neighbour N across it and N's vertex opposite that face."""
+    s = sg.make_config("tiny")
+    m = tmx.Mesh(s.points, s.tets, s.tris, upload=False, faces=True)
+    e = m.export()
+    F = m.export_faces()
+    V, Nb = e["cold"][:, :4], e["cold"][:, 4:]
+    pts = e["points"].reshape(-1, 4)[:, :3]
+    order = np.argsort(V, axis=1, kind="stable")
+    for t in range(len(V)):
+        for r in range(4):
+            j = order[t, r]
+            n = int(Nb[t, j])
+            ent = F[t, r]
+            assert ent[0] == n
+            if n < 0:                       # flagged: constrained face or boundary
+                assert ent[1] == -1
+                continue
+            face = set(V[t]) - {V[t, j]}
+            w = (set(V[n]) - face).pop()
+            assert len(set(V[n]) & face) == 3 and ent[1] == w
+            assert np.array_equal(ent[2:5].view(np.float32), pts[w])
+    with pytest.raises(Exception):
+        tmx.Mesh(s.points, s.tets, s.tris, upload=False).export_faces()
