@@ -55,7 +55,7 @@ sort_chunks_kernel(const BatchDesc *__restrict__ descs, const int4 *__restrict__
                 where = (uint32_t)__ldg(&D.mesh.cface[2 * c].y) >> 6;
             }
             const uint32_t oct = (w1.x < 0.f) | ((w1.y < 0.f) << 1) | ((w1.z < 0.f) << 2);
-            const uint32_t key = ((where & 0x0FFFFFFFu) << 3) | oct;
+            const uint32_t key = ((where & 0x0FFFFFFFu) << 3) | oct;    // place, then direction class
             v = ((unsigned long long)key << 32) | (unsigned)i;
         }
         s[i] = v;

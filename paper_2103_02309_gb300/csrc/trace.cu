@@ -678,12 +678,13 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 const uint32_t next = (uint32_t)fa.x;
                 uint32_t code = next;
                 bool done = false;
-                if (next & TM_CFACE_FLAG) {
+                if (next >= (uint32_t)(MULTI ? sdesc[m].mesh.nt : mv0.nt)) {
+                    // flagged values (bit 31) end the walk; other ids past the end are corrupt
                     done = true;
-                } else if (next >= (uint32_t)(MULTI ? sdesc[m].mesh.nt : mv0.nt)) {
-                    done = true;
-                    code = TM_BOUNDARY;
-                    sc.flags |= TM_HIT_BAD_ID;
+                    if (!(next & TM_CFACE_FLAG)) {
+                        code = TM_BOUNDARY;
+                        sc.flags |= TM_HIT_BAD_ID;
+                    }
                 } else if (steps >= P.max_steps) {
                     done = true;
                     code = TM_BOUNDARY;
@@ -697,8 +698,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     done = true;
                     code = TM_BOUNDARY;
                 } else {
-                    S.prev = S.tet;
-                    S.tet = (int32_t)next;
+                    S.tet = (int32_t)next;  // (the face-entry walk needs no previous tet)
                     S.i3 = fa.y;
                     const float4 x3 = make_float4(__int_as_float(fa.z), __int_as_float(fa.w),
                                                   __int_as_float(fb.x), 0.f);

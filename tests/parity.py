@@ -1,6 +1,6 @@
 """Comparison of CUDA hits against the FP64 oracle (shared by the GPU tests).
 
-Tolerances (spec bar, scene extent E = 1):
+Tolerances (the parity bar of this project, scene extent E = 1):
 * triangle id identical for >= 99.999 % of rays; a mismatch is excused only
   when the hit that one side reports lies within 1e-6 * E of an edge of its
   triangle (the near-edge tie of the two arithmetics);
