@@ -42,7 +42,8 @@ constexpr int kMaxBatch = 64;
 // The hit slot between the phases, 8 words:
 //   [0] phase (0: walk from here, 1: ended, 2: parked at tet [1] for a re-decided step)
 //   [1] tet (walk: tet to enter; ended: last tet)
-//   [2] prev (walk) or the flagged value that ended the walk (ended)
+//   [2] walk: prev (Tet16 and the paper's other records) or the fourth vertex
+//       of tet [1] (face entries); ended: the flagged value that ended the walk
 //   [3..5] entry face ids, counter-clockwise in the ray's basis  [6] steps  [7] flags
 __device__ __forceinline__ void put_record(tm_hit *hp, int phase, int32_t tet, uint32_t prev_or_code,
                                            int32_t i0, int32_t i1, int32_t i2, uint32_t steps,
@@ -74,6 +75,7 @@ struct PhaseParams {
     const int64_t *n_dev;
     float tau_rel;             // sign-test guard threshold relative to the mesh extent
     const int32_t *stop_tet;   // point-light rays: DEVICE id of the light's tet, else null
+    int slot_i3;               // walk record word 2 = the next tet's fourth vertex (face entries)
 };
 
 // The light's tet of a shadow launch, or -1 (none, or not a tet of the mesh).
@@ -141,7 +143,7 @@ __device__ __noinline__ int32_t search_start(const MeshView mv, const tm_ray *rp
 // Phase 1 for one ray.
 template <int MODE>
 __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
-                                          float tau_rel, int32_t stop_tet) {
+                                          float tau_rel, int32_t stop_tet, bool slot_i3) {
     typedef typename RealOf<MODE>::T R;
     const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(rp));
     const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(rp) + 1);
@@ -210,7 +212,12 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
         put_end(hp, S.prev, next, steps, sc.flags);
     else if ((int32_t)next == stop_tet)
         put_end(hp, (int32_t)next, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
-    else
+    else if (slot_i3) {
+        // the face-entry walk starts from the next tet's fourth vertex
+        const int4 cv = __ldg(mv.cold + 2 * (int64_t)next);
+        const int32_t i3 = cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2;
+        put_record(hp, 0, (int32_t)next, (uint32_t)i3, S.i0, S.i1, S.i2, steps, sc.flags);
+    } else
         put_record(hp, 0, (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
 }
 
@@ -226,9 +233,9 @@ start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
         if (MULTI) {
             const Slot s = find_slot(descs, n_meshes, (unsigned long long)r);
             const BatchDesc &D = descs[s.m];
-            start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel, -1);
+            start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel, -1, P.slot_i3 != 0);
         } else {
-            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, stop);
+            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, stop, P.slot_i3 != 0);
         }
     }
 }
@@ -514,7 +521,12 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
                 return;
             }
         }
-        put_record(hp, 0, (int32_t)next, (uint32_t)S.tet, S.i0, S.i1, S.i2, steps, sc.flags);
+        uint32_t w2 = (uint32_t)S.tet;
+        if (FMT == TM_FORMAT_FACE) {  // the next tet's fourth vertex, as the start phase writes it
+            const int4 cv = __ldg(mv.cold + 2 * (int64_t)next);
+            w2 = (uint32_t)(cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2);
+        }
+        put_record(hp, 0, (int32_t)next, w2, S.i0, S.i1, S.i2, steps, sc.flags);
     }
 }
 
@@ -633,10 +645,8 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     }
                 }
                 if (FMT == TM_FORMAT_FACE && active) {
-                    // the fourth vertex of the tet entered, from its full record
-                    int4 cv, cn;
-                    load32((MULTI ? sdesc[m].mesh.cold : mv0.cold) + 2 * (int64_t)S.tet, cv, cn);
-                    S.i3 = cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2;
+                    // the fourth vertex of the tet entered (written by the start phase)
+                    S.i3 = a.z;
                     if ((uint32_t)S.i3 >= (uint32_t)(MULTI ? sdesc[m].mesh.np : mv0.np)) {
                         put_end(hp, S.tet, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_ID);
                         active = false;
@@ -660,7 +670,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 // since entering the tet, then one 32-byte read ----
                 const uint32_t sig = step_signs<MODE, MODE == FP32G, false>(S, S.p3, S.i3, S.m3, sc);
                 if (MODE == FP32G && sig == kParked) {
-                    put_record(hp, 2, S.tet, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
+                    put_record(hp, 2, S.tet, (uint32_t)S.i3, S.i0, S.i1, S.i2, steps, sc.flags);
                     active = false;
                     parked = true;
                     continue;
@@ -820,6 +830,7 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     P.n_dev = W.n_dev;
     P.tau_rel = W.tau_rel;
     P.stop_tet = MULTI ? nullptr : W.stop_tet;
+    P.slot_i3 = FMT == TM_FORMAT_FACE;
     const int sms = sm_count_cached();
     int64_t g = (W.n_cap + 255) / 256;
     const int64_t gmax = (int64_t)sms * 16;

@@ -29,7 +29,11 @@ def dev(a):
 
 
 class Case:
-    def __init__(self, tmx, scene, order="hilbert", faces=False):
+    """A scene with its oracle mesh and its device mesh.  Device meshes carry
+    face entries by default, so the walk runs the format the library picks
+    for itself (the others are compared with it in test_record_formats_identical)."""
+
+    def __init__(self, tmx, scene, order="hilbert", faces=True):
         self.s = scene
         self.om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
         self.mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, order=order, faces=faces)
@@ -67,9 +71,9 @@ def device_hits(tmx, c, w):
     return h, side
 
 
-def camera_case(tmx, name, n_override=None, order="hilbert"):
+def camera_case(tmx, name, n_override=None, order="hilbert", faces=True):
     s = sg.make_config(name, n_override=n_override)
-    c = Case(tmx, s, order)
+    c = Case(tmx, s, order, faces=faces)
     eye = np.array([s.camera.eye], np.float32)
     c.cam_in, mb = c.om.locate(eye)
     assert mb[0] > 1e-9
@@ -82,7 +86,7 @@ def tiny(tmx):
     return camera_case(tmx, "tiny")
 
 
-def random_case(tmx, n, seed, frac=0.3, jitter=0.2, faces=False):
+def random_case(tmx, n, seed, frac=0.3, jitter=0.2, faces=True):
     pts, tets = sg.freudenthal_grid(n, jitter, seed)
     inside = np.random.default_rng(seed).random((n, n, n)) < frac
     tris = sg.constrained_faces(n, inside)
