@@ -319,6 +319,7 @@ def run_ours(args, world, rank, local):
     guard_rate = float(((g1["flags"] & tmx.HIT_GUARD) != 0).mean())
     fl = np.concatenate([g1["flags"], g2["flags"]])
     slow_rate = float(((fl & tmx.HIT_SLOW_PASS) != 0).mean())
+    retest_rate = float(((fl & tmx.HIT_GUARD) != 0).mean())
     final64_rate = float(((np.concatenate([g1["flags"], g2["flags"]]) & tmx.HIT_FINAL_FP64) != 0).mean())
     value = world * rays_per_step / (ms * 1e-3) / 1e6
     extra = {}
@@ -380,7 +381,8 @@ def run_ours(args, world, rank, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between steps (256 MiB write outside the step events)",
                        "build_s": round(build_s, 2),
-                       "guard_rate_primary": guard_rate, "slow_pass_rate": slow_rate,
+                       "guard_rate_primary": guard_rate, "guard_rate_all": retest_rate,
+                       "parked_rate": slow_rate,
                        "final_fp64_rate": final64_rate, **extra},
             "roofline": roofline, "arms": arms, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
