@@ -52,8 +52,8 @@ RAY_BYTES, HIT_BYTES = 32, 32
 # point; per ray its start record (32 B, in the hit slot), the ray (32 B),
 # the three entry-face points (48 B) and the end record (32 B).
 WALK_RAY_BYTES = 32 + RAY_BYTES + 3 * 16 + 32
-RECORD_BYTES = {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32, "face": 32}
-POINT_BYTES = {"face": 0}   # face entries carry the new vertex; the others read a float4 point
+RECORD_BYTES = {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32, "face": 32, "face16": 16}
+POINT_BYTES = {"face": 0, "face16": 0}   # face entries carry the new vertex; the others read a point
 # Rays generated from each hit: (rays per hit, tmax); None = per-ray (shadow)
 SECONDARY = {"bounce": (1, float("inf")), "ao": (8, 0.05), "shadow": (1, None),
              "reflect": (1, float("inf")), "refract": (1, float("inf"))}
@@ -67,13 +67,13 @@ WORKLOADS = {
                       "bounce per hit", per_hit=1, tmax=float("inf"), kind="bounce"),
     "precision": dict(desc="128^3-cell Kuhn grid (12,582,912 tets, 2,146,689 points, jitter 0.15), "
                            "64 random spheres, 2048x2048 primary rays + 1 cosine bounce per hit",
-                      per_hit=1, tmax=float("inf"), kind="bounce"),
+                      per_hit=1, tmax=float("inf"), kind="bounce", format="face16"),
     "medium": dict(desc="64^3-cell Kuhn grid (1,572,864 tets), 16 random spheres, 1920x1080 "
                         "primary rays + 1 cosine bounce per hit",
                    per_hit=1, tmax=float("inf"), kind="bounce"),
     "large": dict(desc="256^3-cell Kuhn grid (100,663,296 tets), 256 random spheres, 1024x1024 "
                        "primary rays + 8 ambient-occlusion rays per hit (t_max 0.05)",
-                  per_hit=8, tmax=0.05, kind="ao"),
+                  per_hit=8, tmax=0.05, kind="ao", format="face"),
     "batched": dict(desc="32 meshes of 16^3..96^3 cells with 4-32 random spheres each, 1K-2M rays "
                          "per mesh (log-uniform), half camera rays and half uniform-direction rays "
                          "from located interior points", per_hit=0, tmax=float("inf"), kind="none"),
@@ -88,9 +88,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="precision")
     p.add_argument("--order", choices=["hilbert", "input", "hilbert_regions"], default="hilbert")
-    p.add_argument("--format", choices=sorted(RECORD_BYTES), default="face",
-                   help="tet record the walk reads (face entries: the library's automatic choice "
-                        "when the mesh has them)")
+    p.add_argument("--format", choices=sorted(RECORD_BYTES), default=None,
+                   help="tet record the walk reads (default: the faster face-entry layout for the "
+                        "workload, measured: face16 for precision, face for large)")
     p.add_argument("--secondary", choices=sorted(SECONDARY), default=None,
                    help="rays generated from the primary hits (default: the workload's)")
     p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
@@ -224,6 +224,8 @@ def run_ours(args, world, rank, local):
     from paper_2103_02309_gb300.shard import max_over_ranks
 
     W = dict(WORKLOADS[args.workload])
+    if args.format is None:
+        args.format = W.get("format", "face16")
     kind = args.secondary or W["kind"]
     if kind != W["kind"]:
         W["per_hit"], W["tmax"] = SECONDARY[kind]
@@ -231,12 +233,14 @@ def run_ours(args, world, rank, local):
     s = build_scene(args.workload)
     t0 = time.time()
     mesh = tmx.Mesh(s.points, s.tets, s.tris, order=args.order,
-                    tet20=args.format.startswith("tet20"), faces=args.format == "face")
+                    tet20=args.format.startswith("tet20"), faces=args.format == "face",
+                    faces16=args.format == "face16")
     build_s = time.time() - t0
     cam = tmx.make_camera(s.camera.eye, s.camera.fov_deg, s.camera.width, s.camera.height)
     n_primary = s.camera.width * s.camera.height
     per_hit = W["per_hit"]
-    default_run = (kind == WORKLOADS[args.workload]["kind"] and args.format == "face"
+    default_run = (kind == WORKLOADS[args.workload]["kind"]
+                   and args.format == WORKLOADS[args.workload].get("format", "face16")
                    and args.order == "hilbert")
     dev = torch.device("cuda", local)
     eye = torch.tensor([s.camera.eye], dtype=torch.float32, device=dev)
@@ -257,8 +261,10 @@ def run_ours(args, world, rank, local):
         e.record(stream)                                  # materialise the CUDA events
     torch.cuda.synchronize()
 
-    def opts(mode, ev=None):
-        bounded = W["tmax"] is not None and math.isfinite(W["tmax"])
+    def opts(mode, ev=None, secondary=False):
+        # early exit at t_max for the secondary rays with a finite t_max only
+        # (primary rays are unbounded)
+        bounded = secondary and W["tmax"] is not None and math.isfinite(W["tmax"])
         return tmx.trace_opts(mode=mode, block=args.block, refill=args.refill,
                               batch_steps=args.batch_steps, tmax_early_exit=bounded,
                               phase_events=ev, format=args.format)
@@ -280,7 +286,7 @@ def run_ours(args, world, rank, local):
             mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
 
     def timed(mode, steps, warmup):
-        op, ob = opts(mode, ev_p), opts(mode, ev_b)
+        op, ob = opts(mode, ev_p), opts(mode, ev_b, secondary=True)
         for _ in range(warmup):
             step(op, ob)
         torch.cuda.synchronize()
@@ -421,7 +427,8 @@ def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world, f
             hits_host=torch.empty((m, 8), dtype=torch.int32).pin_memory(),
             hits2_host=torch.empty((m * per_hit, 8), dtype=torch.int32).pin_memory(),
             count_host=torch.empty(1, dtype=torch.int64).pin_memory()))
-    o = tmx.trace_opts(mode="fp32g", tmax_early_exit=math.isfinite(W["tmax"]), format=fmt)
+    o = tmx.trace_opts(mode="fp32g", format=fmt)
+    o2 = tmx.trace_opts(mode="fp32g", tmax_early_exit=math.isfinite(W["tmax"]), format=fmt)
     main = torch.cuda.current_stream(dev)
 
     def step():
@@ -435,7 +442,7 @@ def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world, f
                 mesh.trace(ch["rays"], hits=ch["hits"], opts=o, stream=st)
                 mesh.gen_secondary(ch["hits"], per_hit, W["tmax"], seed=0x5EED + c,
                                    rays_out=ch["rays2"], count=ch["count"], stream=st)
-                mesh.trace(ch["rays2"], hits=ch["hits2"], n_dev=ch["count"], opts=o, stream=st)
+                mesh.trace(ch["rays2"], hits=ch["hits2"], n_dev=ch["count"], opts=o2, stream=st)
                 ch["hits_host"].copy_(ch["hits"], non_blocking=True)
                 ch["hits2_host"].copy_(ch["hits2"], non_blocking=True)
                 ch["count_host"].copy_(ch["count"], non_blocking=True)
@@ -573,7 +580,7 @@ def run_batched(args, world, rank, local):
     for dsc in descs:
         s = sg.make_grid_scene("batched", dsc["n"], sg.BATCHED["jitter"], dsc["seed"],
                                n_spheres=dsc["n_spheres"])
-        mesh = tmx.Mesh(s.points, s.tets, s.tris, faces=True)
+        mesh = tmx.Mesh(s.points, s.tets, s.tris, faces=True, faces16=True)
         n_prim = dsc["primary"]
         side = max(1, int(math.ceil(math.sqrt(n_prim))))
         cam = tmx.make_camera(sg.BATCHED["camera_eye"], sg.BATCHED["fov_deg"], side,

@@ -79,7 +79,8 @@ enum { TM_ORDER_HILBERT = 0, TM_ORDER_INPUT = 1, TM_ORDER_HILBERT_REGIONS = 2 };
  * one int32[5] per tet at a 20-B stride); Tet32 = the full record V0..V3,
  * N0..N3 (32 B, the mesh's cold records, so it needs no extra memory; Alg. 3
  * with VX = V0^V1^V2^V3).  All give identical hits.  TM_FORMAT_AUTO (0)
- * selects the face entries below when the mesh has them, else Tet32: on
+ * selects the 16-byte face entries below when the mesh has them, else the
+ * 32-byte ones, else Tet32: on
  * GB300 the walk is bound by instruction issue and cache latency, not by
  * HBM bandwidth, a 32-byte record costs one 32-byte sector like a 16-byte
  * one, and the full record needs the fewest instructions to decode.
@@ -91,14 +92,19 @@ enum { TM_ORDER_HILBERT = 0, TM_ORDER_INPUT = 1, TM_ORDER_HILBERT_REGIONS = 2 };
  * of N's vertex opposite that face (W = -1 when N is flagged).  A step then
  * needs one 32-byte read, issued as soon as the exit face is known, instead
  * of a record read followed by a dependent point read; it costs 128 B per
- * tet.  Batches take Tet16, Tet32, packed Tet20 or face entries. */
+ * tet.  TM_FORMAT_FACE16 (needs tm_build_opts.faces16, at most 2^29 tets)
+ * halves them: entry r is {N | w << 29, x, y, z} (16 B), with w the rank of
+ * W among N's vertex ids in bits 29-30 of a tet value; the walk then tracks
+ * the ranks of its face vertices instead of their ids.  Batches take Tet16,
+ * Tet32, packed Tet20 or either face layout. */
 enum {
     TM_FORMAT_AUTO = 0,
     TM_FORMAT_TET16 = 1,
     TM_FORMAT_TET20 = 2,
     TM_FORMAT_TET32 = 3,
     TM_FORMAT_TET20_AOS = 4,
-    TM_FORMAT_FACE = 5
+    TM_FORMAT_FACE = 5,
+    TM_FORMAT_FACE16 = 6
 };
 
 /* A ray, 32 bytes, two 16-byte words.
@@ -150,6 +156,7 @@ typedef struct {
     int32_t fix_orientation; /* nonzero: swap V2,V3 of tets with orient3d < 0 instead of failing */
     int32_t tet20;           /* nonzero: also pack the Tet20 records, split and packed (40 B per tet) */
     int32_t faces;           /* nonzero: also pack the face entries of TM_FORMAT_FACE (128 B per tet) */
+    int32_t faces16;         /* nonzero: also pack those of TM_FORMAT_FACE16 (64 B per tet) */
 } tm_build_opts;
 
 typedef struct {
@@ -184,6 +191,7 @@ typedef struct {
     const void *tet20_n3_dev;    /* int32[n_tets] N3, or NULL */
     const void *tet20_aos_dev;   /* int32[5*n_tets] (VX, N0, N1, N2, N3), or NULL */
     const void *face_dev;        /* int32[32*n_tets] face entries (TM_FORMAT_FACE), or NULL */
+    const void *face16_dev;      /* int32[16*n_tets] face entries (TM_FORMAT_FACE16), or NULL */
     int64_t device_bytes;        /* bytes the mesh holds on the device */
     int64_t n_regions;           /* regions found by TM_ORDER_HILBERT_REGIONS, else 0 */
 } tm_mesh_info;
@@ -229,6 +237,9 @@ tm_status tm_mesh_export_tet20(const tm_mesh *mesh, int32_t *vxn, int32_t *n3, i
  * (the position words as float32 bit patterns).  TM_ERR_ARG if the mesh was
  * built without them. */
 tm_status tm_mesh_export_faces(const tm_mesh *mesh, int32_t *faces);
+
+/* The same for the 16-byte entries: faces16 int32[n_tets*16]. */
+tm_status tm_mesh_export_faces16(const tm_mesh *mesh, int32_t *faces16);
 
 enum { TM_IDS_TET = 0, TM_IDS_POINT = 1 };
 enum { TM_TO_INPUT = 0, TM_TO_INTERNAL = 1 };

@@ -41,7 +41,8 @@ f64 = ctypes.c_double
 
 
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("order", i32), ("fix_orientation", i32), ("tet20", i32), ("faces", i32)]
+    _fields_ = [("order", i32), ("fix_orientation", i32), ("tet20", i32), ("faces", i32),
+                ("faces16", i32)]
 
 
 class TraceOpts(ctypes.Structure):
@@ -54,7 +55,7 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("n_points", i64), ("n_tets", i64), ("n_tris", i64), ("extent", f64),
                 ("bbox_lo", f32 * 3), ("bbox_hi", f32 * 3), ("source_tet", i32),
                 ("on_device", i32), ("tet16_dev", P), ("points_dev", P), ("cold_dev", P),
-                ("cface_dev", P), ("tet20_dev", P), ("tet20_n3_dev", P), ("tet20_aos_dev", P), ("face_dev", P),
+                ("cface_dev", P), ("tet20_dev", P), ("tet20_n3_dev", P), ("tet20_aos_dev", P), ("face_dev", P), ("face16_dev", P),
                 ("device_bytes", i64), ("n_regions", i64)]
 
 
@@ -75,6 +76,7 @@ _SIGS = {
     "tm_mesh_export": ([P, P, P, P, P, P, P], ctypes.c_int),
     "tm_mesh_export_tet20": ([P, P, P, P], ctypes.c_int),
     "tm_mesh_export_faces": ([P, P], ctypes.c_int),
+    "tm_mesh_export_faces16": ([P, P], ctypes.c_int),
     "tm_map_ids": ([P, ctypes.c_int, ctypes.c_int, P, P, i64], ctypes.c_int),
     "tm_hilbert_keys": ([P, i64, ctypes.c_int, P], ctypes.c_int),
     "tm_locate": ([P, P, i64, P, i32, P, P], ctypes.c_int),

@@ -194,14 +194,18 @@ tm_status tm_batch_set(tm_batch *b, const tm_ray *const *rays, const int64_t *n,
     }
     b->cfg = resolve_trace_opts(opts, max_nt);
     if (b->cfg.format == TM_FORMAT_AUTO) {
-        bool all_faces = true;
-        for (const tm_mesh *m : b->meshes) all_faces = all_faces && m->d_face;
-        b->cfg.format = auto_format(all_faces);
+        bool all_faces = true, all_faces16 = true;
+        for (const tm_mesh *m : b->meshes) {
+            all_faces = all_faces && m->d_face;
+            all_faces16 = all_faces16 && m->d_face16;
+        }
+        b->cfg.format = auto_format(all_faces16, all_faces);
     }
     if (b->cfg.format == TM_FORMAT_TET20) return TM_ERR_ARG;  // two arrays per mesh: not batched
     for (const tm_mesh *m : b->meshes) {
         if (b->cfg.format == TM_FORMAT_TET20_AOS && !m->d_t20aos) return TM_ERR_ARG;
         if (b->cfg.format == TM_FORMAT_FACE && !m->d_face) return TM_ERR_ARG;
+        if (b->cfg.format == TM_FORMAT_FACE16 && !m->d_face16) return TM_ERR_ARG;
     }
     b->sort_chunk = sort_chunk;
     b->n_chunks = (int64_t)chunks.size();
@@ -277,9 +281,12 @@ tm_status tm_batch_autotune(tm_batch *b, int reps, tm_tuned *best, void *stream)
     const int refills[] = {4, 8, 16, 24, 32};
     const int steps[] = {2, 4, 8, 16, 32};
     const int chunks[] = {0, 256, 1024, 4096};
-    bool all_faces = true;
-    for (const tm_mesh *m : b->meshes) all_faces = all_faces && m->d_face;
-    const int formats[] = {all_faces ? TM_FORMAT_FACE : TM_FORMAT_TET32, TM_FORMAT_TET32, TM_FORMAT_TET16};
+    bool all_faces = true, all_faces16 = true;
+    for (const tm_mesh *m : b->meshes) {
+        all_faces = all_faces && m->d_face;
+        all_faces16 = all_faces16 && m->d_face16;
+    }
+    const int formats[] = {auto_format(all_faces16, all_faces), TM_FORMAT_TET32, TM_FORMAT_TET16};
     for (int pass = 0; pass < 2 && st == TM_OK; ++pass) {
         for (int v : formats) {
             tm_trace_opts c = o; c.format = v; float ms;

@@ -183,6 +183,8 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
     const bool fix = opts ? opts->fix_orientation != 0 : false;
     const bool want_t20 = opts ? opts->tet20 != 0 : false;
     const bool want_face = opts ? opts->faces != 0 : false;
+    const bool want_face16 = opts ? opts->faces16 != 0 : false;
+    if (want_face16 && nt > (int64_t(1) << 29)) return TM_ERR_TOO_LARGE;  // tet ids share a word with w
     if (order != TM_ORDER_HILBERT && order != TM_ORDER_INPUT && order != TM_ORDER_HILBERT_REGIONS)
         return TM_ERR_ARG;
     m->np = np;
@@ -449,6 +451,34 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
             }
         }
     }
+    if (want_face16) {
+        // entry r of tet T: the neighbour N across the face opposite T's
+        // vertex of rank r, the rank w of N's opposite vertex W among N's
+        // vertex ids (bits 29-30), and W's position
+        m->face16.assign((size_t)nt * 16, 0);
+#pragma omp parallel for schedule(static)
+        for (int64_t tn = 0; tn < nt; ++tn) {
+            const int32_t *V = &m->cold[8 * tn];
+            const int32_t *NB = &m->cold[8 * tn + 4];
+            int idx[4] = {0, 1, 2, 3};
+            std::sort(idx, idx + 4, [&](int x, int y) { return V[x] < V[y]; });
+            for (int r = 0; r < 4; ++r) {
+                int32_t *e = &m->face16[16 * tn + 4 * r];
+                const uint32_t nb = (uint32_t)NB[idx[r]];
+                e[0] = (int32_t)nb;
+                if (nb & TM_CFACE_FLAG) continue;
+                const int32_t *V2 = &m->cold[8 * (int64_t)nb];
+                const int32_t *N2 = &m->cold[8 * (int64_t)nb + 4];
+                for (int j = 0; j < 4; ++j)
+                    if (N2[j] == (int32_t)tn) {
+                        const int32_t w = V2[j];
+                        const uint32_t wr = (uint32_t)((V2[0] < w) + (V2[1] < w) + (V2[2] < w) + (V2[3] < w));
+                        e[0] = (int32_t)(nb | (wr << 29));
+                        std::memcpy(&e[1], &m->pts4[4 * (int64_t)w], 3 * sizeof(float));
+                    }
+            }
+        }
+    }
     m->cface.resize((size_t)nc * 8);
 #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c) {
@@ -520,6 +550,11 @@ tm_status tm_upload(tm_mesh *m) {
                            cudaMemcpyHostToDevice));
         m->device_bytes += (int64_t)(40 * m->nt);
     }
+    if (!m->face16.empty()) {
+        TM_CUDA(cudaMalloc(&m->d_face16, 64 * (size_t)m->nt));
+        TM_CUDA(cudaMemcpy(m->d_face16, m->face16.data(), 64 * (size_t)m->nt, cudaMemcpyHostToDevice));
+        m->device_bytes += (int64_t)(64 * m->nt);
+    }
     if (!m->face.empty()) {
         TM_CUDA(cudaMalloc(&m->d_face, 128 * (size_t)m->nt));
         TM_CUDA(cudaMemcpy(m->d_face, m->face.data(), 128 * (size_t)m->nt, cudaMemcpyHostToDevice));
@@ -574,6 +609,8 @@ void tm_free_device(tm_mesh *m) {
     cudaFree(m->d_t20aos);
     cudaFree(m->d_face);
     m->d_face = nullptr;
+    cudaFree(m->d_face16);
+    m->d_face16 = nullptr;
     m->d_t20 = nullptr;
     m->d_t20n3 = nullptr;
     m->d_t20aos = nullptr;

@@ -102,6 +102,7 @@ tm_status tm_mesh_info_get(const tm_mesh *m, tm_mesh_info *info) {
     info->tet20_n3_dev = m->d_t20n3;
     info->tet20_aos_dev = m->d_t20aos;
     info->face_dev = m->d_face;
+    info->face16_dev = m->d_face16;
     info->device_bytes = m->device_bytes;
     info->n_regions = m->n_regions;
     return TM_OK;
@@ -130,6 +131,12 @@ tm_status tm_mesh_export_tet20(const tm_mesh *m, int32_t *vxn, int32_t *n3, int3
 tm_status tm_mesh_export_faces(const tm_mesh *m, int32_t *faces) {
     if (!m || m->face.empty() || !faces) return TM_ERR_ARG;
     std::memcpy(faces, m->face.data(), sizeof(int32_t) * m->face.size());
+    return TM_OK;
+}
+
+tm_status tm_mesh_export_faces16(const tm_mesh *m, int32_t *faces16) {
+    if (!m || m->face16.empty() || !faces16) return TM_ERR_ARG;
+    std::memcpy(faces16, m->face16.data(), sizeof(int32_t) * m->face16.size());
     return TM_OK;
 }
 
@@ -172,6 +179,7 @@ tm_status tm_trace(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_
     if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
     if (cfg.format == TM_FORMAT_TET20_AOS && !m->d_t20aos) return TM_ERR_ARG;
     if (cfg.format == TM_FORMAT_FACE && !m->d_face) return TM_ERR_ARG;
+    if (cfg.format == TM_FORMAT_FACE16 && !m->d_face16) return TM_ERR_ARG;
     return launch_trace(mesh_view(m), rays, n, n_dev, hits, cfg, (cudaStream_t)stream);
 }
 
@@ -185,6 +193,7 @@ tm_status tm_trace_shadow(const tm_mesh *m, const tm_ray *rays, int64_t n, const
     if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
     if (cfg.format == TM_FORMAT_TET20_AOS && !m->d_t20aos) return TM_ERR_ARG;
     if (cfg.format == TM_FORMAT_FACE && !m->d_face) return TM_ERR_ARG;
+    if (cfg.format == TM_FORMAT_FACE16 && !m->d_face16) return TM_ERR_ARG;
     cfg.bounded = true;
     cfg.stop_tet = light_tet_dev;
     return launch_trace(mesh_view(m), rays, n, n_dev, hits, cfg, (cudaStream_t)stream);

@@ -30,6 +30,7 @@ struct tm_mesh {
     std::vector<int32_t> t20n3;  // nt: N3, when built
     std::vector<int32_t> t20aos; // nt*5: VX, N0..N3 at a 20-byte stride, when built
     std::vector<int32_t> face;   // nt*32: four face entries {N, W, x, y, z, 0, 0, 0}, when built
+    std::vector<int32_t> face16; // nt*16: four face entries {N | w << 29, x, y, z}, when built
     std::vector<int32_t> pperm, tperm;  // internal -> input
     std::vector<int32_t> pinv, tinv;    // input -> internal
     // device copies
@@ -44,6 +45,7 @@ struct tm_mesh {
     int32_t *d_t20n3 = nullptr;
     int32_t *d_t20aos = nullptr;
     int4 *d_face = nullptr;
+    int4 *d_face16 = nullptr;
     int64_t device_bytes = 0;
     int64_t n_regions = 0;  // regions found by TM_ORDER_HILBERT_REGIONS (else 0)
 };
@@ -65,6 +67,7 @@ struct MeshView {
     const int32_t *t20n3;  // Tet20 N3 (may be null)
     const int32_t *t20aos; // Tet20 packed {VX, N0..N3} (may be null)
     const int4 *face;      // face entries, two int4 each, four per tet (may be null)
+    const int4 *face16;    // 16-byte face entries, four per tet (may be null)
     float lo[3], cell_inv;  // lattice origin and kSeedGrid / extent
 };
 
@@ -83,6 +86,7 @@ inline MeshView mesh_view(const tm_mesh *m) {
     v.t20n3 = m->d_t20n3;
     v.t20aos = m->d_t20aos;
     v.face = m->d_face;
+    v.face16 = m->d_face16;
     for (int a = 0; a < 3; ++a) v.lo[a] = m->lo[a];
     v.cell_inv = m->extent > 0 ? (float)(kSeedGrid / m->extent) : 0.f;
     return v;
@@ -112,13 +116,14 @@ struct TraceConfig {
     int batch_steps;
     int ctas_per_sm;
     bool bounded;
+    bool block_auto;  // block not given: 512 threads, 256 for bounded walks (which hold more state)
     cudaEvent_t events[4];
     int format;
     const int32_t *stop_tet;  // point-light rays: DEVICE id of the tet to stop in (null: none); needs bounded
 };
 TraceConfig resolve_trace_opts(const tm_trace_opts *opts, int64_t nt);
 // The record TM_FORMAT_AUTO walks: face entries when the mesh has them, else Tet32.
-int auto_format(bool has_faces);
+int auto_format(bool has_faces16, bool has_faces);
 
 tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const int64_t *n_dev,
                        tm_hit *hits, const TraceConfig &cfg, cudaStream_t s);

@@ -18,7 +18,7 @@ import torch
 from . import _native as N
 
 MODES = {"fp32g": 0, "fp32": 1, "fp64": 2}
-FORMATS = {"auto": 0, "tet16": 1, "tet20": 2, "tet32": 3, "tet20_aos": 4, "face": 5}
+FORMATS = {"auto": 0, "tet16": 1, "tet20": 2, "tet32": 3, "tet20_aos": 4, "face": 5, "face16": 6}
 ORDERS = {"hilbert": 0, "input": 1, "hilbert_regions": 2}
 
 HIT_SIDE_NEG = 0x01
@@ -122,12 +122,12 @@ class Mesh:
     """A compact constrained tet mesh on the current CUDA device."""
 
     def __init__(self, points, tets, tris, order="hilbert", upload=True, fix_orientation=False,
-                 tet20=False, faces=False):
+                 tet20=False, faces=False, faces16=False):
         pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
         tt = np.ascontiguousarray(tets, np.int32).reshape(-1, 4)
         tr = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
         o = N.BuildOpts(ORDERS[order], 1 if fix_orientation else 0, 1 if tet20 else 0,
-                        1 if faces else 0)
+                        1 if faces else 0, 1 if faces16 else 0)
         h = ctypes.c_void_p()
         N.check(N.lib.tm_build(_hptr(pts), len(pts), _hptr(tt), len(tt),
                                _hptr(tr) if len(tr) else None, len(tr), ctypes.byref(o),
@@ -179,6 +179,12 @@ class Mesh:
         """Face entries int32 [n_tets, 4, 8] (see TM_FORMAT_FACE)."""
         f = np.empty((self.n_tets, 4, 8), np.int32)
         N.check(N.lib.tm_mesh_export_faces(self._h, _hptr(f)), "tm_mesh_export_faces")
+        return f
+
+    def export_faces16(self) -> np.ndarray:
+        """16-byte face entries int32 [n_tets, 4, 4] (see TM_FORMAT_FACE16)."""
+        f = np.empty((self.n_tets, 4, 4), np.int32)
+        N.check(N.lib.tm_mesh_export_faces16(self._h, _hptr(f)), "tm_mesh_export_faces16")
         return f
 
     def map_ids(self, kind, direction, ids) -> np.ndarray:

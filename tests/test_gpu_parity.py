@@ -36,7 +36,8 @@ class Case:
     def __init__(self, tmx, scene, order="hilbert", faces=True):
         self.s = scene
         self.om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
-        self.mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, order=order, faces=faces)
+        self.mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, order=order, faces=faces,
+                             faces16=faces)
         e = self.mesh.export()
         self.tperm = e["tet_perm"]
         self.tinv = np.empty_like(self.tperm)
@@ -229,7 +230,7 @@ def test_record_formats_identical(tmx, mode):
             c0 = random_case(tmx, 6, 515)
             scene = c0.s
         om = oracle.OracleMesh(scene.points, scene.tets, scene.tris)
-        mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, tet20=True, faces=True)
+        mesh = tmx.Mesh(scene.points, scene.tets, scene.tris, tet20=True, faces=True, faces16=True)
         tinv = np.empty(scene.n_tets, np.int64)
         tinv[mesh.export()["tet_perm"]] = np.arange(scene.n_tets)
         g = np.random.default_rng(8)
@@ -242,8 +243,8 @@ def test_record_formats_identical(tmx, mode):
             rays = dev(tmx.pack_rays(q[keep], d[keep], tmax, tinv[start[keep]]))
             got = {f: tmx.unpack_hits(mesh.trace(rays, mode=mode, format=f,
                                                  tmax_early_exit=np.isfinite(tmax)))
-                   for f in ("tet16", "tet20", "tet20_aos", "tet32", "face")}
-            for f in ("tet20", "tet20_aos", "tet32", "face"):
+                   for f in ("tet16", "tet20", "tet20_aos", "tet32", "face", "face16")}
+            for f in ("tet20", "tet20_aos", "tet32", "face", "face16"):
                 for k in ("tri", "t", "b1", "b2", "tet", "steps", "flags"):
                     assert np.array_equal(got[f][k], got["tet16"][k]), (f, k)
             w = om.trace(q[keep], d[keep], tmax, start[keep])
@@ -334,7 +335,7 @@ def test_batch_matches_single_launches(tmx, faces):
         data.append((o, d, st))
     b = tmx.Batch([c.mesh for c in cases])
     hits = [torch.empty((r.shape[0], 8), dtype=torch.int32, device="cuda") for r in rays]
-    formats = ["auto", "tet16", "tet32"] + (["face"] if faces else [])
+    formats = ["auto", "tet16", "tet32"] + (["face", "face16"] if faces else [])
     for fmt in formats:
         for chunk in (0, 256):
             for h in hits:

@@ -236,3 +236,24 @@ def test_face_entries(tmx):
             assert np.array_equal(ent[2:5].view(np.float32), pts[w])
     with pytest.raises(Exception):
         tmx.Mesh(s.points, s.tets, s.tris, upload=False).export_faces()
+
+
+def test_face16_entries(tmx):
+    """16-byte face entries: the neighbour, the rank of its opposite vertex among
+    its own ids (bits 29-30), and that vertex's position."""
+    s = sg.make_config("tiny")
+    m = tmx.Mesh(s.points, s.tets, s.tris, upload=False, faces=True, faces16=True)
+    e = m.export()
+    F = m.export_faces()
+    G = m.export_faces16()
+    V = e["cold"][:, :4]
+    for t in range(len(V)):
+        for r in range(4):
+            n, w = int(F[t, r, 0]), int(F[t, r, 1])
+            g = int(G[t, r, 0]) & 0xFFFFFFFF
+            if n < 0:
+                assert g == n & 0xFFFFFFFF
+                continue
+            assert g & 0x1FFFFFFF == n and g >> 31 == 0
+            assert (g >> 29) & 3 == int((V[n] < w).sum())
+            assert np.array_equal(G[t, r, 1:4], F[t, r, 2:5])
