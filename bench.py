@@ -73,7 +73,7 @@ WORKLOADS = {
                    per_hit=1, tmax=float("inf"), kind="bounce"),
     "large": dict(desc="256^3-cell Kuhn grid (100,663,296 tets), 256 random spheres, 1024x1024 "
                        "primary rays + 8 ambient-occlusion rays per hit (t_max 0.05)",
-                  per_hit=8, tmax=0.05, kind="ao", format="face"),
+                  per_hit=8, tmax=0.05, kind="ao", format="face16"),
     "batched": dict(desc="32 meshes of 16^3..96^3 cells with 4-32 random spheres each, 1K-2M rays "
                          "per mesh (log-uniform), half camera rays and half uniform-direction rays "
                          "from located interior points", per_hit=0, tmax=float("inf"), kind="none"),
@@ -89,8 +89,8 @@ def parse():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="precision")
     p.add_argument("--order", choices=["hilbert", "input", "hilbert_regions"], default="hilbert")
     p.add_argument("--format", choices=sorted(RECORD_BYTES), default=None,
-                   help="tet record the walk reads (default: the faster face-entry layout for the "
-                        "workload, measured: face16 for precision, face for large)")
+                   help="tet record the walk reads (default: 16-byte face entries, the "
+                        "library's automatic choice when built)")
     p.add_argument("--secondary", choices=sorted(SECONDARY), default=None,
                    help="rays generated from the primary hits (default: the workload's)")
     p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
