@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtetmesh.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["trace.cu", "locate.cu", "raygen.cu", "batch.cu", "build.cpp", "capi.cpp"]
+SOURCES = ["trace.cu", "locate.cu", "raygen.cu", "batch.cu", "probe.cu", "build.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3",
           f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]

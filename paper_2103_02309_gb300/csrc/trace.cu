@@ -570,19 +570,24 @@ template <int FMT> struct GuardInLoop {
 };
 
 // Guard mode, 16-byte face entries: the walk keeps the ranks of its
-// vertices among the current tet's ids, so the re-test first recovers the
-// ids from the tet's full record, then runs the double-precision triple
-// products (ties broken by ids, which order like the ranks).  Out of line.
-__device__ __noinline__ static uint32_t guard_signs_ranked(const tm_ray *ray, const float4 *pts,
-                                                           const int4 *cold, int32_t tet, float d0,
-                                                           float d1, float d2, float t0, float t1,
-                                                           float t2, int r0, int r1, int r2, int r3) {
+// vertices among the current tet's ids, so the re-test of one sign test
+// (ranks ra = the new vertex, rb = a face vertex) first recovers the ids from
+// the tet's full record.  Returns bit 0 = det(p_a, p_b) > 0 by the
+// double-precision triple product (ties by ids, which order like the ranks),
+// TM_HIT_GUARD / TM_HIT_TIE in bits 8 and up.  Out of line.
+__device__ __noinline__ static uint32_t guard_pair_ranked(const tm_ray *ray, const float4 *pts,
+                                                          const int4 *cold, int32_t tet, int ra,
+                                                          int rb) {
     const int4 cv = __ldg(cold + 2 * (int64_t)tet);
     const int32_t V[4] = {cv.x, cv.y, cv.z, cv.w};
     int32_t id[4] = {0, 0, 0, 0};
     for (int j = 0; j < 4; ++j)
         id[(V[0] < V[j]) + (V[1] < V[j]) + (V[2] < V[j]) + (V[3] < V[j])] = V[j];
-    return guard_signs_impl(ray, pts, d0, d1, d2, t0, t1, t2, id[r0], id[r1], id[r2], id[r3]);
+    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
+    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
+    const double dd = triple(w0, w1, __ldg(pts + id[ra]), __ldg(pts + id[rb]));
+    if (dd != 0.0) return (uint32_t)(dd > 0.0) | (TM_HIT_GUARD << 8);
+    return (uint32_t)(id[ra] < id[rb]) | ((TM_HIT_GUARD | TM_HIT_TIE) << 8);
 }
 #ifndef TM_WALK_MAXREG_FP64
 #define TM_WALK_MAXREG_FP64 72
@@ -732,31 +737,51 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
             if (!active) continue;
             if constexpr (FMT == TM_FORMAT_FACE16) {
                 // ---- one step over 16-byte face entries, on vertex ranks ----
-                const R d0 = det2(S.p3, S.p0), d1 = det2(S.p3, S.p1), d2 = det2(S.p3, S.p2);
-                uint32_t sig = (uint32_t)(d0 > R(0)) | ((uint32_t)(d1 > R(0)) << 1) |
-                               ((uint32_t)(d2 > R(0)) << 2);
                 const uint32_t PR = (uint32_t)S.i0;  // packed ranks (PackedRanks)
                 const int q0 = PackedRanks<MODE>::value ? (int)(PR & 0xffu) : S.i0;
                 const int q1 = PackedRanks<MODE>::value ? (int)((PR >> 8) & 0xffu) : S.i1;
                 const int q2 = PackedRanks<MODE>::value ? (int)((PR >> 16) & 0xffu) : S.i2;
                 const int q3 = PackedRanks<MODE>::value ? (int)(PR >> 24) : S.i3;
+                int e;
+                if constexpr (MODE == FP32G) {
+                // Alg. 1 reads two sign tests: det(p3, p0), then det(p3, p1) when it
+                // is positive, det(p3, p2) otherwise; only those two are guarded
+                const R d0 = det2(S.p3, S.p0);
+                bool s0 = d0 > R(0);
                 if (MODE == FP32G) {
-                    const float t0 = fmaxf(S.m3, S.m0), t1 = fmaxf(S.m3, S.m1), t2 = fmaxf(S.m3, S.m2);
-                    if (!(fabsf((float)d0) > t0) | !(fabsf((float)d1) > t1) | !(fabsf((float)d2) > t2)) {
-                        const uint32_t r = guard_signs_ranked(
-                            sc.ray, pts, MULTI ? sdesc[m].mesh.cold : mv0.cold, S.tet, (float)d0,
-                            (float)d1, (float)d2, t0, t1, t2, q0, q1, q2, q3);
+                    if (!(fabsf((float)d0) > fmaxf(S.m3, S.m0))) {
+                        const uint32_t r = guard_pair_ranked(sc.ray, pts, MULTI ? sdesc[m].mesh.cold : mv0.cold,
+                                                             S.tet, q3, q0);
                         sc.flags |= r >> 8;
-                        sig = r & 7u;
+                        s0 = r & 1u;
                     }
-                } else if ((d0 == R(0)) | (d1 == R(0)) | (d2 == R(0))) {
-                    // exact zeros: ranks order like the ids they stand for
+                }
+                const P2<R> pk = s0 ? S.p1 : S.p2;
+                const R dk = det2(S.p3, pk);
+                bool sk = dk > R(0);
+                if (MODE == FP32G) {
+                    if (!(fabsf((float)dk) > fmaxf(S.m3, s0 ? S.m1 : S.m2))) {
+                        const uint32_t r = guard_pair_ranked(sc.ray, pts, MULTI ? sdesc[m].mesh.cold : mv0.cold,
+                                                             S.tet, q3, s0 ? q1 : q2);
+                        sc.flags |= r >> 8;
+                        sk = r & 1u;
+                    }
+                }
+                e = s0 ? (sk ? 0 : 2) : (sk ? 1 : 0);
+                } else {
+                // unguarded: the three sign tests, exact zeros broken by ranks
+                // (they order like the ids they stand for)
+                const R d0 = det2(S.p3, S.p0), d1 = det2(S.p3, S.p1), d2 = det2(S.p3, S.p2);
+                uint32_t sig = (uint32_t)(d0 > R(0)) | ((uint32_t)(d1 > R(0)) << 1) |
+                               ((uint32_t)(d2 > R(0)) << 2);
+                if ((d0 == R(0)) | (d1 == R(0)) | (d2 == R(0))) {
                     sc.flags |= TM_HIT_TIE;
                     if (d0 == R(0)) sig |= (uint32_t)(q3 < q0);
                     if (d1 == R(0)) sig |= (uint32_t)(q3 < q1) << 1;
                     if (d2 == R(0)) sig |= (uint32_t)(q3 < q2) << 2;
                 }
-                const int e = exit_slot_bits(sig);
+                e = exit_slot_bits(sig);
+                }
                 const int re = PackedRanks<MODE>::value ? (int)((PR >> (8 * e)) & 0xffu)
                                                : (e == 0 ? S.i0 : (e == 1 ? S.i1 : S.i2));
                 const int4 f = __ldg(recs + 4 * (int64_t)S.tet + re);

@@ -292,74 +292,62 @@ __device__ __noinline__ static int2 step3d(const MeshView &mv, const tm_ray *ray
     return make_int2((int)nb, skip_next);
 }
 
-// Guard mode: the three sign tests of one step when at least one of them is
-// within its threshold (or exactly zero), re-decided by the double-precision
-// triple product of the two points (ties broken by vertex ids).  Out of line:
-// the rare path.  Returns the three signs in bits 0..2 and TM_HIT_GUARD /
-// TM_HIT_TIE in bits 8 and up.
-__device__ __forceinline__ uint32_t guard_signs_impl(const tm_ray *ray, const float4 *pts, float d0,
-                                                     float d1, float d2, float t0, float t1, float t2,
-                                                     int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
-    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
-    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
-    const float4 x3 = __ldg(pts + i3);
-    const float d[3] = {d0, d1, d2}, t[3] = {t0, t1, t2};
-    const int32_t id[3] = {i0, i1, i2};
-    uint32_t bits = 0, flags = 0;
-    for (int k = 0; k < 3; ++k) {
-        bool pos;
-        if (fabsf(d[k]) > t[k]) {
-            pos = d[k] > 0.f;
-        } else {
-            flags |= TM_HIT_GUARD;
-            const double dd = triple(w0, w1, x3, __ldg(pts + id[k]));
-            if (dd != 0.0) {
-                pos = dd > 0.0;
-            } else {
-                flags |= TM_HIT_TIE;
-                pos = i3 < id[k];
-            }
-        }
-        bits |= (uint32_t)pos << k;
-    }
-    return bits | (flags << 8);
-}
-__device__ __noinline__ static uint32_t guard_signs(const tm_ray *ray, const float4 *pts, float d0,
-                                                    float d1, float d2, float t0, float t1, float t2,
-                                                    int32_t i0, int32_t i1, int32_t i2, int32_t i3) {
-    return guard_signs_impl(ray, pts, d0, d1, d2, t0, t1, t2, i0, i1, i2, i3);
-}
-
-// The three sign tests of one step, det(p3, p_k) > 0 for the entry-face
-// slots k = 0, 1, 2 (bit k), with the same decision rule as pos().  In guard
-// mode with PARK, a step with an ambiguous test is not decided: the function
-// returns kParked and the caller hands the ray to the slow pass; INLINE_GUARD
-// inlines the double-precision re-test instead of calling it.
+// The sign tests of one step, det(p3, p_k) > 0 for the entry-face slots
+// k = 0, 1, 2 (bit k), with the same decision rule as pos().  In guard mode
+// only the two tests Alg. 1 reads are made (and guarded); with PARK a step
+// with an ambiguous one is not decided: the function returns kParked and the
+// caller hands the ray to the slow pass; INLINE_GUARD inlines the
+// double-precision re-test instead of calling it.
 constexpr uint32_t kParked = 0xffffffffu;
+
+// Guard mode: the double-precision decision of one sign test det(p_a, p_b)
+// (ties broken by ids), with TM_HIT_GUARD / TM_HIT_TIE added to *flags.
+template <bool INLINE>
+__device__ __forceinline__ bool guard_one(const tm_ray *ray, const float4 *pts, int32_t ia, int32_t ib,
+                                          uint32_t &flags) {
+    double dd;
+    if (INLINE) {
+        const float4 w0 = __ldg(reinterpret_cast<const float4 *>(ray));
+        const float4 w1 = __ldg(reinterpret_cast<const float4 *>(ray) + 1);
+        dd = triple(w0, w1, __ldg(pts + ia), __ldg(pts + ib));
+    } else {
+        dd = guard_det(ray, pts, ia, ib);
+    }
+    flags |= TM_HIT_GUARD;
+    if (dd != 0.0) return dd > 0.0;
+    flags |= TM_HIT_TIE;
+    return ia < ib;
+}
 
 template <int MODE, bool PARK, bool INLINE_GUARD, class R>
 __device__ __forceinline__ uint32_t step_signs(const WalkState<R> &S, const P2<R> &p3, int32_t i3,
                                                float m3, SignCtx &c) {
+    if (MODE == FP32G) {
+        // Alg. 1 reads two sign tests: det(p3, p0), then det(p3, p1) when it is
+        // positive, det(p3, p2) otherwise; only those two are guarded.  The
+        // bits returned give exit_slot_bits() the same slot.
+        const R d0 = det2(p3, S.p0);
+        bool s0 = d0 > R(0);
+        if (!(fabsf((float)d0) > fmaxf(m3, S.m0))) {
+            if (PARK) return kParked;
+            s0 = guard_one<INLINE_GUARD>(c.ray, c.pts, i3, S.i0, c.flags);
+        }
+        const P2<R> pk = s0 ? S.p1 : S.p2;
+        const R dk = det2(p3, pk);
+        bool sk = dk > R(0);
+        if (!(fabsf((float)dk) > fmaxf(m3, s0 ? S.m1 : S.m2))) {
+            if (PARK) return kParked;
+            sk = guard_one<INLINE_GUARD>(c.ray, c.pts, i3, s0 ? S.i1 : S.i2, c.flags);
+        }
+        return s0 ? (1u | ((uint32_t)sk << 1)) : ((uint32_t)sk << 2);
+    }
     const R d0 = det2(p3, S.p0), d1 = det2(p3, S.p1), d2 = det2(p3, S.p2);
     uint32_t bits = (uint32_t)(d0 > R(0)) | ((uint32_t)(d1 > R(0)) << 1) | ((uint32_t)(d2 > R(0)) << 2);
-    if (MODE == FP32G) {
-        const float t0 = fmaxf(m3, S.m0), t1 = fmaxf(m3, S.m1), t2 = fmaxf(m3, S.m2);
-        const bool amb = !(fabsf((float)d0) > t0) | !(fabsf((float)d1) > t1) | !(fabsf((float)d2) > t2);
-        if (amb) {
-            if (PARK) return kParked;
-            const uint32_t r = INLINE_GUARD
-                ? guard_signs_impl(c.ray, c.pts, (float)d0, (float)d1, (float)d2, t0, t1, t2, S.i0, S.i1, S.i2, i3)
-                : guard_signs(c.ray, c.pts, (float)d0, (float)d1, (float)d2, t0, t1, t2, S.i0, S.i1, S.i2, i3);
-            c.flags |= r >> 8;
-            bits = r & 7u;
-        }
-    } else {
-        if ((d0 == R(0)) | (d1 == R(0)) | (d2 == R(0))) {
-            c.flags |= TM_HIT_TIE;
-            if (d0 == R(0)) bits |= (uint32_t)(i3 < S.i0);
-            if (d1 == R(0)) bits |= (uint32_t)(i3 < S.i1) << 1;
-            if (d2 == R(0)) bits |= (uint32_t)(i3 < S.i2) << 2;
-        }
+    if ((d0 == R(0)) | (d1 == R(0)) | (d2 == R(0))) {
+        c.flags |= TM_HIT_TIE;
+        if (d0 == R(0)) bits |= (uint32_t)(i3 < S.i0);
+        if (d1 == R(0)) bits |= (uint32_t)(i3 < S.i1) << 1;
+        if (d2 == R(0)) bits |= (uint32_t)(i3 < S.i2) << 2;
     }
     return bits;
 }
