@@ -135,11 +135,20 @@ def measured_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_code(text):
+    """Source text without comments and blank space, so that a comment edit
+    does not mark a profile of the same code as stale."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.strip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("trace.cu", "walk.cuh"):  # the walk kernel's sources
-        with open(os.path.join(ROOT, "paper_2103_02309_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2103_02309_gb300", "csrc", f)) as fh:
+            h.update(kernel_code(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

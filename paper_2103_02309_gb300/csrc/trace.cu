@@ -5,31 +5,37 @@
 //     with at most four 2-D triangle tests (Sec. 4), or the restart through a
 //     hit face into the tet on its arrival side (Sec. 6).  It leaves a walk
 //     record in the ray's own hit slot.
-//  2. walk_kernel, persistent: the per-tet step (Alg. 6 / Alg. 7 with Alg. 1)
-//     until a flagged (constrained or boundary) neighbour; it leaves an end
-//     record in the hit slot.  Each step reads one 16-byte Tet16 record and
-//     one 16-byte point:
-//       idx3 = idx0 ^ idx1 ^ idx2 ^ VX
-//       ra = rank of idx3, rb = rank of idx_exit among the four vertex ids
-//       N3 = ra == 3 ? prev : prev ^ NX_ra ;  next = rb == 3 ? N3 : N3 ^ NX_rb
+//  2. walk_kernel, persistent: the per-tet step (Alg. 1 on the new vertex,
+//     then the neighbour across the exit face) until a flagged (constrained
+//     or boundary) neighbour; it leaves an end record in the hit slot.  The
+//     step reads one of the paper's records (Sec. 3), each with the float4
+//     point of the new vertex:
+//       Tet16 (Alg. 6-7): idx3 = idx0 ^ idx1 ^ idx2 ^ VX;
+//         ra = rank of idx3, rb = rank of idx_exit among the four vertex ids;
+//         N3 = ra == 3 ? prev : prev ^ NX_ra ;  next = rb == 3 ? N3 : N3 ^ NX_rb
+//       Tet20 (Alg. 4-5): next = N[rb];  Tet32 (Alg. 2-3): next = N across idx_exit
+//     or this library's face entries, which hold the neighbour across each
+//     face together with the neighbour's new vertex, so a step is one read
+//     issued once the exit face is known (16-byte entries keep the vertices'
+//     ranks among the tet's ids instead of the ids).
 //     Lanes whose ray ended are refilled from a global cursor once `refill`
 //     lanes are idle (ballot + popc, one atomicAdd per warp, ids handed out
 //     by rank within the idle mask), so the rays of one grab are consecutive
 //     and warps stay full (the persistent-threads scheme of Aila & Laine,
 //     "Understanding the efficiency of ray traversal on GPUs", HPG 2009).
-//     In guard mode the walk decides every sign test in float32; at a step
-//     where a test falls within the guard threshold the lane writes the ray's
-//     state back to its hit slot ("parks" it), and at its next refill it
-//     re-decides that one step out of line with the double-precision
-//     re-test, then continues from the new record.  No walk state is live
-//     across that call, so the step loop keeps a small register budget.
+//     In guard mode the walk makes the two sign tests Alg. 1 reads in
+//     float32 and re-decides one that falls within the guard threshold in
+//     double precision: the face-entry walks in the loop through an
+//     out-of-line call; the walks over the paper's records park the ray in
+//     its hit slot and re-decide the step at the lane's next refill, with no
+//     walk state live across that call.
 //  3. finish_kernel, one thread per ray: the ray-triangle test on the hit
 //     triangle in its own vertex order, with the FP64 guard, into the hit.
 //
 // Keeping the once-per-ray work out of the walk kernel keeps the walk's
-// register state small (no spills) and its code free of calls except the
-// rare FP64 re-test.  The hit slot (32 bytes per ray) carries the state
-// between the phases, so no scratch memory is needed beyond the cursor.
+// register state small and its code free of calls except the rare FP64
+// re-test.  The hit slot (32 bytes per ray) carries the state between the
+// phases, so no scratch memory is needed beyond the cursor.
 #include <cmath>
 
 #include "walk.cuh"
