@@ -48,6 +48,8 @@ def _bind(lib):
     lib.orc_mesh_create.argtypes = [i64, P, i64, P, i64, P, ctypes.POINTER(P)]
     lib.orc_mesh_create.restype = ctypes.c_int
     lib.orc_mesh_destroy.argtypes = [P]
+    lib.orc_soup_create.argtypes = [i64, P, i64, P, ctypes.POINTER(P)]
+    lib.orc_soup_create.restype = ctypes.c_int
     lib.orc_mesh_arrays.argtypes = [P, P, P, P]
     for f in ("orc_count_nonpositive", "orc_count_asymmetric", "orc_count_boundary"):
         getattr(lib, f).argtypes = [P]
@@ -179,3 +181,27 @@ class OracleMesh:
         w = np.empty(4)
         self.lib.orc_tet_bary(self._h, int(t), _ptr(q), _ptr(w))
         return w
+
+
+class OracleTriangles(OracleMesh):
+    """Points and triangles without tets: only `bruteforce` (the plain
+    definition of the hit, nearest triangle over all of them) is available.
+    For scenes whose tet adjacency is too large to build on the host."""
+
+    def __init__(self, points, tris, lib=None):
+        self.lib = lib or load()
+        self.points = np.ascontiguousarray(points, dtype=np.float32)
+        self.tets = np.zeros((0, 4), np.int32)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+        h = ctypes.c_void_p()
+        st = self.lib.orc_soup_create(len(self.points), _ptr(self.points), len(self.tris),
+                                      _ptr(self.tris), ctypes.byref(h))
+        if st != 0:
+            raise OracleError(_STATUS.get(st, f"status {st}"))
+        self._h = h
+
+    def _tetless(self, *a, **k):
+        raise OracleError("a triangle set has no tets")
+
+    trace = locate = arrays = tet_bary = _tetless
+    count_nonpositive = count_asymmetric = count_boundary = _tetless

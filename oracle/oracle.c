@@ -198,6 +198,30 @@ fail:
     return status;
 }
 
+void orc_mesh_destroy(orc_mesh *m);
+
+/* A triangle set without tets: points and constrained triangles only, for
+ * orc_bruteforce on scenes too large for the adjacency build (no walk,
+ * location or checker may be called on it).  Status as orc_mesh_create. */
+int orc_soup_create(int64_t np, const float *pts, int64_t nc, const int32_t *tris,
+                    orc_mesh **out) {
+    *out = NULL;
+    if (np <= 0 || nc < 0) return 1;
+    orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
+    if (!m) return 5;
+    m->np = np; m->nc = nc;
+    m->P = (double *)malloc(sizeof(double) * 3 * np);
+    m->tri = (int32_t *)malloc(sizeof(int32_t) * 3 * (nc > 0 ? nc : 1));
+    if (!m->P || !m->tri) { orc_mesh_destroy(m); return 5; }
+    for (int64_t i = 0; i < 3 * np; ++i) m->P[i] = (double)pts[i];
+    for (int64_t i = 0; i < 3 * nc; ++i) {
+        if (tris[i] < 0 || tris[i] >= np) { orc_mesh_destroy(m); return 1; }
+        m->tri[i] = tris[i];
+    }
+    *out = m;
+    return 0;
+}
+
 void orc_mesh_destroy(orc_mesh *m) {
     if (!m) return;
     free(m->P); free(m->T); free(m->tri); free(m->nbr); free(m->nbrk); free(m->fc); free(m->ctet);

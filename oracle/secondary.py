@@ -115,6 +115,23 @@ def hit_side(ctet: np.ndarray, hit_tri: np.ndarray, hit_tet: np.ndarray) -> np.n
     return side
 
 
+def arrival_side(points, tris, hit_tri, d) -> np.ndarray:
+    """Side (0 = +, 1 = -) from which each ray of direction d arrives at its
+    hit triangle, from the geometry alone: a ray travelling against the
+    normal (v1-v0)x(v2-v0) comes from the side the normal points to.  Equals
+    hit_side for every hit that is not tangent to its triangle; needs no tets."""
+    P = np.asarray(points, dtype=np.float64)
+    tris = np.asarray(tris)
+    hit_tri = np.asarray(hit_tri)
+    side = np.zeros(len(hit_tri), dtype=np.int32)
+    ok = hit_tri >= 0
+    c = hit_tri[ok].astype(np.int64)
+    v0, v1, v2 = P[tris[c, 0]], P[tris[c, 1]], P[tris[c, 2]]
+    nd = (np.cross(v1 - v0, v2 - v0) * np.asarray(d, dtype=np.float64)[ok]).sum(1)
+    side[ok] = np.where(nd < 0.0, 0, 1)
+    return side
+
+
 def _hit_points(points, tris, hit_tri, hit_b1, hit_b2):
     """Selected hit rows, triangle ids, hit points, first vertices and unnormalised normals (FP64)."""
     P = np.asarray(points, dtype=np.float64)

@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from oracle.secondary import mix64, secondary_rays, hit_side, uniform, GAMMA, M64
+from oracle.secondary import arrival_side, mix64, secondary_rays, hit_side, uniform, GAMMA, M64
 
 ROOT_GOLDEN = __file__.rsplit("/", 1)[0] + "/golden"
 
@@ -246,6 +246,25 @@ def test_restart_rays_equal_bruteforce():
     b3 = m.bruteforce(o3, d3, tm3, exclude=entry3 >> 1)
     compare_walk_brute(pts, tris, w3, b3, tol=1e-7)
     assert (w3["t"][w3["tri"] >= 0] <= 0.05).all()
+
+
+def test_triangle_set_bruteforce_and_arrival_side():
+    """The tet-free triangle set (for scenes too large for the adjacency
+    build) finds the walk's hits, and the side a ray arrives from, taken from
+    the geometry alone, is the side of the tet the walk ends in."""
+    pts, tets, tris = random_scene(5, 57, frac=0.35)
+    m = oracle.OracleMesh(pts, tets, tris)
+    ts = oracle.OracleTriangles(pts, tris)
+    q, d, start = random_rays(m, 3000, 57)
+    w = m.trace(q, d, np.inf, start)
+    b = ts.bruteforce(q, d, np.inf)
+    assert compare_walk_brute(pts, tris, w, b, tol=1e-7) > 0.995
+    hit = w["tri"] >= 0
+    assert hit.sum() > 1000
+    _, _, ctet = m.arrays()
+    np.testing.assert_array_equal(arrival_side(pts, tris, w["tri"], d), hit_side(ctet, w["tri"], w["tet"]))
+    with pytest.raises(oracle.OracleError):
+        ts.trace(q, d, np.inf, start)
 
 
 def test_locate_contains_point():
