@@ -163,7 +163,8 @@ typedef struct {
     int32_t mode;        /* TM_MODE_* */
     float guard_tau;     /* relative guard threshold; <= 0 selects 1e-6 */
     uint32_t max_steps;  /* walk bound per ray; 0 selects 4*n_tets^(1/3)*8 + 256 */
-    int32_t block;       /* threads per block: 0 (auto), 64..1024, multiple of 32 */
+    int32_t block;       /* threads per block: 0 (auto: two blocks an SM at the walk's register
+                            budget), 64..1024, multiple of 32 */
     int32_t refill;      /* refill a warp once this many lanes are idle: 0 (auto), 1..32 */
     int32_t batch_steps; /* walk steps between refill checks: 0 (auto), 1..256 */
     int32_t ctas_per_sm; /* persistent CTAs per SM: 0 (as many as fit) */

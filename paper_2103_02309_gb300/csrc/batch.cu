@@ -277,7 +277,7 @@ tm_status tm_batch_autotune(tm_batch *b, int reps, tm_tuned *best, void *stream)
     };
     float best_ms = 0.f;
     tm_status st = measure(o, chunk, &best_ms);
-    const int blocks[] = {128, 256, 512};
+    const int blocks[] = {128, 256, 384, 512, 576};
     const int refills[] = {4, 8, 16, 24, 32};
     const int steps[] = {2, 4, 8, 16, 32};
     const int chunks[] = {0, 256, 1024, 4096};

@@ -116,7 +116,7 @@ struct TraceConfig {
     int batch_steps;
     int ctas_per_sm;
     bool bounded;
-    bool block_auto;  // block not given: 512 threads, 256 for bounded walks (which hold more state)
+    bool block_auto;  // block not given: two blocks an SM at the walk's register budget
     cudaEvent_t events[4];
     int format;
     const int32_t *stop_tet;  // point-light rays: DEVICE id of the tet to stop in (null: none); needs bounded

@@ -227,8 +227,15 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
         put_record(hp, 0, (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
 }
 
+#ifndef TM_START_MIN_BLOCKS
+#define TM_START_MIN_BLOCKS 1
+#endif
+#ifndef TM_FINISH_MIN_BLOCKS
+#define TM_FINISH_MIN_BLOCKS 1
+#endif
+
 template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, TM_START_MIN_BLOCKS)
 start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
              tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
              const __grid_constant__ PhaseParams P) {
@@ -307,7 +314,7 @@ __device__ __forceinline__ void finish_one(const MeshView &mv, const tm_ray *rp,
 }
 
 template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, TM_FINISH_MIN_BLOCKS)
 finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
               tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
               const __grid_constant__ PhaseParams P) {
@@ -544,11 +551,12 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
 }
 
 // Register budget per thread of the walk (float32; the FP64 arm keeps
-// double-width state).  Set by measurement on GB300: at 512 threads per
-// block an SM holds two blocks at 48 or at 64 registers alike, and 64 keeps
-// the guard mode's state out of local memory.
+// double-width state).  An SM's 65,536 registers hold 36 warps at 56
+// registers a thread against 32 at 64; measured on GB300, the extra warps
+// hide more of the bounce rays' record latency (bounce walk -8 %) and cost
+// the guard mode a few bytes of spill.  48 registers spill more and lose.
 #ifndef TM_WALK_MAXREG
-#define TM_WALK_MAXREG 64
+#define TM_WALK_MAXREG 56
 #endif
 // Guard mode: the face-entry walk re-decides an ambiguous step in the loop
 // with the out-of-line double-precision triple product (1); the walks over
@@ -598,16 +606,31 @@ __device__ __noinline__ static uint32_t guard_pair_ranked(const tm_ray *ray, con
 #ifndef TM_WALK_MAXREG_FP64
 #define TM_WALK_MAXREG_FP64 72
 #endif
-// Bounded walks (early exit at t_max) carry the ray's depth state as well:
-// 80 registers at 256 threads per block measured 3 % faster on short
-// ambient-occlusion rays than 64 registers at 512.
+// Bounded walks (early exit at t_max) carry the ray's depth state as well.
+// On short ambient-occlusion rays 64 registers (32 warps an SM) measured
+// 13 % faster than 80 (24 warps) and 4 % faster than 72 or 56.
 #ifndef TM_WALK_MAXREG_BOUNDED
-#define TM_WALK_MAXREG_BOUNDED 80
+#define TM_WALK_MAXREG_BOUNDED 64
 #endif
 
+constexpr int walk_maxreg(int mode, bool bounded) {
+    return mode == FP64 ? TM_WALK_MAXREG_FP64 : (bounded ? TM_WALK_MAXREG_BOUNDED : TM_WALK_MAXREG);
+}
+
+// Default threads per block: two blocks an SM with as many warps as the
+// register budget allows (65,536 registers an SM, 64 warps at most):
+// 576 threads at 56 registers, 512 at 64.  The double-precision arm is
+// bound by the FP64 pipe instead: 512 threads (one block, 16 warps an SM at
+// 72 registers) measured 2 % faster than two blocks of 448.
+int walk_default_block(int mode, bool bounded) {
+    if (mode == FP64) return 512;
+    int warps = 65536 / (walk_maxreg(mode, bounded) * 32);
+    if (warps > 64) warps = 64;
+    return warps / 2 * 32;
+}
+
 template <int MODE, int FMT, bool BOUNDED, bool MULTI>
-__global__ void __maxnreg__(MODE == FP64 ? TM_WALK_MAXREG_FP64
-                            : (BOUNDED ? TM_WALK_MAXREG_BOUNDED : TM_WALK_MAXREG))
+__global__ void __maxnreg__(walk_maxreg(MODE, BOUNDED))
 walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
             tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
             const __grid_constant__ WalkParams P) {
@@ -1088,12 +1111,12 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.tau = (o && o->guard_tau > 0.f) ? o->guard_tau : 1e-6f;
     const double side = std::cbrt((double)(nt > 0 ? nt : 1));
     c.max_steps = (o && o->max_steps) ? o->max_steps : (uint32_t)(4.0 * side * 8.0 + 256.0);
-    c.block_auto = !(o && o->block);
-    c.block = c.block_auto ? 512 : o->block;
     c.refill = (o && o->refill) ? o->refill : 8;
     c.batch_steps = (o && o->batch_steps) ? o->batch_steps : 16;
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
+    c.block_auto = !(o && o->block);
+    c.block = c.block_auto ? walk_default_block(c.mode, c.bounded) : o->block;
     for (int i = 0; i < 4; ++i) c.events[i] = o ? (cudaEvent_t)o->phase_events[i] : nullptr;
     c.format = o ? o->format : TM_FORMAT_AUTO;  // resolved against the mesh at launch
     c.stop_tet = nullptr;
@@ -1118,7 +1141,7 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
                        tm_hit *hits, const TraceConfig &cfg_in, cudaStream_t s) {
     TraceConfig cfg = cfg_in;
     if (cfg.format == TM_FORMAT_AUTO) cfg.format = auto_format(mv.face16 != nullptr, mv.face != nullptr);
-    if (cfg.block_auto && cfg.bounded) cfg.block = 256;
+    if (cfg.block_auto) cfg.block = walk_default_block(cfg.mode, cfg.bounded);
     if (!valid_config(cfg)) return TM_ERR_ARG;
     if (n == 0) return TM_OK;
     if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
