@@ -227,15 +227,22 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
         put_record(hp, 0, (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
 }
 
+// The start phase chases three or four dependent reads per ray (the ray,
+// its restart face, the tet's record and points, the next tet's record) and
+// is latency-bound: capped at 64 registers it runs four blocks of 256 an SM
+// instead of two, with some spill on its rare paths, and measured 20 %
+// faster on bounce and ambient-occlusion rays.  (The double-precision arm,
+// whose state is twice as wide, keeps its registers.)  The finish phase
+// gained nothing from the same change.
 #ifndef TM_START_MIN_BLOCKS
-#define TM_START_MIN_BLOCKS 1
+#define TM_START_MIN_BLOCKS 4
 #endif
 #ifndef TM_FINISH_MIN_BLOCKS
 #define TM_FINISH_MIN_BLOCKS 1
 #endif
 
 template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, TM_START_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, MODE == FP64 ? 1 : TM_START_MIN_BLOCKS)
 start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
              tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
              const __grid_constant__ PhaseParams P) {
