@@ -389,8 +389,11 @@ def run_ours(args, world, rank, local):
                           "ms_per_step": round(ams, 3), "trace_ms": round(atr, 3),
                           "walk_ms": round(awk, 3)}
             if mode == "fp64":
-                a1 = tmx.unpack_hits(hits)["tri"]
-                arms[mode]["primary_id_agreement_vs_fp32g"] = float((a1 == g1["tri"]).mean())
+                a = tmx.unpack_hits(hits)
+                arms[mode]["primary_id_agreement_vs_fp32g"] = float((a["tri"] == g1["tri"]).mean())
+                both = (a["tri"] == g1["tri"]) & (a["tri"] >= 0)
+                rel = np.abs(g1["t"][both].astype(np.float64) - a["t"][both]) / np.abs(a["t"][both])
+                arms[mode]["primary_max_rel_t_fp32g_vs_fp64"] = float(rel.max()) if both.any() else 0.0
         arms["fp32g_speedup_vs_fp64"] = round(value / arms["fp64"]["value"], 2)
         hits.copy_(keep[0])
 
@@ -523,18 +526,26 @@ def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world, f
 # CPU oracle (baseline leg and reference arm)
 
 
-def oracle_step(om, s, W, cam_tet, sel, nthreads):
-    """One step of the workload on the host oracle for the pixels `sel`; returns rays traced."""
+def oracle_step(om, s, W, cam_tet, sel, nthreads, brute=False):
+    """One step of the workload on the host oracle for the pixels `sel`; returns rays traced.
+    brute: nearest triangle over all of them instead of the walk (tiny scenes only)."""
     import scenegen as sg
-    from oracle.secondary import hit_side, secondary_rays
+    from oracle.secondary import arrival_side, hit_side, secondary_rays
     o, d = sg.camera_rays(s.camera)
     o, d = o[sel], d[sel]
-    w = om.trace(o, d, np.inf, cam_tet, nthreads=nthreads)
-    ctet = om.ctet_cache if hasattr(om, "ctet_cache") else om.arrays()[2]
-    side = hit_side(ctet, w["tri"], w["tet"])
+    if brute:
+        w = om.bruteforce(o, d, np.inf, nthreads=nthreads)
+        side = arrival_side(s.points, s.tris, w["tri"], d)
+    else:
+        w = om.trace(o, d, np.inf, cam_tet, nthreads=nthreads)
+        ctet = om.ctet_cache if hasattr(om, "ctet_cache") else om.arrays()[2]
+        side = hit_side(ctet, w["tri"], w["tet"])
     o2, d2, tm2, entry, _ = secondary_rays(s.points, s.tris, w["tri"], w["b1"], w["b2"], side,
                                            0x5EED, W["per_hit"], W["tmax"], ray_ids=sel)
-    om.trace(o2, d2, tm2, -1, entry, nthreads=nthreads)
+    if brute:
+        om.bruteforce(o2, d2, tm2, exclude=entry >> 1, nthreads=nthreads)
+    else:
+        om.trace(o2, d2, tm2, -1, entry, nthreads=nthreads)
     return len(o) + len(o2)
 
 
@@ -579,6 +590,17 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
     t1 = time.time()
     traced1 = oracle_step(om, s, W, cam_tet[0], one, 1)
     dt1 = time.time() - t1
+    brute = None
+    if workload == "tiny":
+        # brute force over all triangles, the oracle's other route to the same hits
+        allpix = np.arange(n)
+        t2 = time.time()
+        tb = oracle_step(om, s, W, cam_tet[0], allpix, nthreads, brute=True)
+        db = time.time() - t2
+        brute = {"value": round(tb / db / 1e6, 4), "unit": UNIT, "cores": nthreads,
+                 "sample": f"the whole {s.camera.width}x{s.camera.height} image + its {W['kind']} "
+                           f"rays, Moller-Trumbore against all {s.n_tris} triangles; {tb} rays "
+                           f"in {db:.2f} s"}
     return {"value": round(traced / dt / 1e6, 4), "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"every {stride}th pixel of the {s.camera.width}x{s.camera.height} image "
                       f"({len(sel)} primary rays) + their {W['kind']} rays"
@@ -588,7 +610,8 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
             "single_core": {"value": round(traced1 / dt1 / 1e6, 4), "unit": UNIT, "cores": 1,
                             "sample": f"every {stride1}th pixel "
                                       f"({len(one)} primary rays) + their {W['kind']} rays; "
-                                      f"{traced1} rays in {dt1:.1f} s"}}
+                                      f"{traced1} rays in {dt1:.1f} s"},
+            **({"bruteforce": brute} if brute else {})}
 
 
 def run_reference(args, world, rank):
