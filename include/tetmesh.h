@@ -315,7 +315,9 @@ tm_status tm_gen_primary(const tm_camera *cam, const int32_t *start_dev, float t
  * order into DEVICE rays_out (capacity n*per_hit), the count is written to
  * DEVICE *count_dev (int64), and src_out (DEVICE int32, may be NULL) gets the
  * index i of each ray's hit.  hits may hold n_dev (DEVICE int64, may be
- * NULL) valid entries instead of n. */
+ * NULL) valid entries instead of n.  A hit whose cface is not a constrained
+ * face of this mesh (0 <= cface < n_tris fails: a foreign or corrupted
+ * record) counts as a miss here and in the other generators. */
 tm_status tm_gen_secondary(const tm_mesh *mesh, const tm_hit *hits, int64_t n,
                            const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                            tm_ray *rays_out, int64_t *count_dev, int32_t *src_out, void *stream);

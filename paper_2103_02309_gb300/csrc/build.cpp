@@ -492,6 +492,18 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
         r[6] = m->pinv[(size_t)tris[3 * c + 2]];
         r[7] = 0;
     }
+    // the hit kernels' view of a triangle: its three vertices inline (one
+    // 48-byte read instead of the record and three point reads)
+    m->cgeo.resize((size_t)nc * 12);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nc; ++c) {
+        int32_t *g = &m->cgeo[12 * c];
+        for (int k = 0; k < 3; ++k)
+            std::memcpy(&g[4 * k], &m->pts4[4 * (int64_t)m->cface[8 * c + 4 + k]], 3 * sizeof(float));
+        g[3] = m->cface[8 * c + 1];
+        g[7] = (int32_t)c;
+        g[11] = 0;
+    }
 
     // default locate source: the tet whose centroid is nearest the box centre
     const double cen[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
@@ -523,12 +535,14 @@ tm_status tm_upload(tm_mesh *m) {
     TM_CUDA(cudaGetDevice(&m->device));
     const size_t b_tet = sizeof(int4) * (size_t)m->nt, b_pts = sizeof(float4) * (size_t)m->np,
                  b_cold = 2 * sizeof(int4) * (size_t)m->nt,
-                 b_cf = 2 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1);
+                 b_cf = 2 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1),
+                 b_cg = 3 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1);
     cudaError_t e;
     if ((e = cudaMalloc(&m->d_tet16, b_tet)) != cudaSuccess ||
         (e = cudaMalloc(&m->d_pts, b_pts)) != cudaSuccess ||
         (e = cudaMalloc(&m->d_cold, b_cold)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_cface, b_cf)) != cudaSuccess) {
+        (e = cudaMalloc(&m->d_cface, b_cf)) != cudaSuccess ||
+        (e = cudaMalloc(&m->d_cgeo, b_cg)) != cudaSuccess) {
         tm_set_error("cudaMalloc", e);
         return e == cudaErrorMemoryAllocation ? TM_ERR_OOM : TM_ERR_CUDA;
     }
@@ -538,7 +552,10 @@ tm_status tm_upload(tm_mesh *m) {
     if (m->nc > 0)
         TM_CUDA(cudaMemcpy(m->d_cface, m->cface.data(), 2 * sizeof(int4) * (size_t)m->nc,
                            cudaMemcpyHostToDevice));
-    m->device_bytes = (int64_t)(b_tet + b_pts + b_cold + b_cf);
+    if (m->nc > 0)
+        TM_CUDA(cudaMemcpy(m->d_cgeo, m->cgeo.data(), 3 * sizeof(int4) * (size_t)m->nc,
+                           cudaMemcpyHostToDevice));
+    m->device_bytes = (int64_t)(b_tet + b_pts + b_cold + b_cf + b_cg);
     if (!m->t20.empty()) {
         TM_CUDA(cudaMalloc(&m->d_t20, sizeof(int4) * (size_t)m->nt));
         TM_CUDA(cudaMalloc(&m->d_t20n3, sizeof(int32_t) * (size_t)m->nt));
@@ -602,6 +619,8 @@ void tm_free_device(tm_mesh *m) {
     cudaFree(m->d_pts);
     cudaFree(m->d_cold);
     cudaFree(m->d_cface);
+    cudaFree(m->d_cgeo);
+    m->d_cgeo = nullptr;
     cudaFree(m->d_seeds);
     m->d_seeds = nullptr;
     cudaFree(m->d_t20);

@@ -58,12 +58,18 @@ __device__ __forceinline__ int64_t valid_count(int64_t n, const int64_t *n_dev) 
     return n_dev ? min(n, *n_dev) : n;
 }
 
+// A hit the generators use: a triangle id, on a constrained face of this
+// mesh (a foreign or corrupted record counts as a miss, never as an index).
+__device__ __forceinline__ bool usable_hit(int32_t tri, int32_t cface, int32_t nc) {
+    return tri >= 0 && (uint32_t)cface < (uint32_t)nc;
+}
+
 __global__ void __launch_bounds__(kScanBlock)
-count_hits_kernel(const tm_hit *__restrict__ hits, int64_t n, const int64_t *n_dev,
+count_hits_kernel(const tm_hit *__restrict__ hits, int64_t n, const int64_t *n_dev, int32_t nc,
                   int32_t *__restrict__ block_counts) {
     const int64_t nv = valid_count(n, n_dev);
     const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    const bool hit = i < nv && __ldg(&hits[i].tri) >= 0;
+    const bool hit = i < nv && usable_hit(__ldg(&hits[i].tri), __ldg(&hits[i].cface), nc);
     const int c = __syncthreads_count(hit);
     if (threadIdx.x == 0) block_counts[blockIdx.x] = c;
 }
@@ -113,7 +119,7 @@ struct HitIn {
     int4 h0, h1;
     bool hit;
 };
-__device__ __forceinline__ HitIn load_hit(const tm_hit *hits, int64_t i, int64_t nv) {
+__device__ __forceinline__ HitIn load_hit(const tm_hit *hits, int64_t i, int64_t nv, int32_t nc) {
     HitIn r;
     r.h0 = make_int4(-1, 0, 0, 0);
     r.h1 = make_int4(0, 0, 0, 0);
@@ -121,7 +127,7 @@ __device__ __forceinline__ HitIn load_hit(const tm_hit *hits, int64_t i, int64_t
         r.h0 = __ldcs(reinterpret_cast<const int4 *>(hits + i));
         r.h1 = __ldcs(reinterpret_cast<const int4 *>(hits + i) + 1);
     }
-    r.hit = r.h0.x >= 0;
+    r.hit = usable_hit(r.h0.x, r.h1.y, nc);
     return r;
 }
 
@@ -150,8 +156,11 @@ struct HitGeom {
 __device__ __forceinline__ HitGeom hit_geometry(const MeshView &mv, const HitIn &h) {
     HitGeom g;
     const int32_t c = h.h1.y;
-    const int4 cr = __ldg(mv.cface + 2 * c + 1);
-    const float4 a = __ldg(mv.pts + cr.x), b = __ldg(mv.pts + cr.y), d = __ldg(mv.pts + cr.z);
+    const int4 g0 = __ldg(mv.cgeo + 3 * c), g1 = __ldg(mv.cgeo + 3 * c + 1),
+               g2 = __ldg(mv.cgeo + 3 * c + 2);
+    const float4 a = make_float4(__int_as_float(g0.x), __int_as_float(g0.y), __int_as_float(g0.z), 0.f);
+    const float4 b = make_float4(__int_as_float(g1.x), __int_as_float(g1.y), __int_as_float(g1.z), 0.f);
+    const float4 d = make_float4(__int_as_float(g2.x), __int_as_float(g2.y), __int_as_float(g2.z), 0.f);
     const float b1 = __int_as_float(h.h0.z), b2 = __int_as_float(h.h0.w);
     const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
     const float e2x = d.x - a.x, e2y = d.y - a.y, e2z = d.z - a.z;
@@ -178,7 +187,7 @@ emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restr
                       int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
                       int32_t *__restrict__ src) {
     const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    const HitIn h = load_hit(hits, i, valid_count(n, n_dev));
+    const HitIn h = load_hit(hits, i, valid_count(n, n_dev), mv.nc);
     const int64_t pos = hit_position(h.hit, offsets);
     if (!h.hit) return;
     const int32_t c = h.h1.y;
@@ -218,7 +227,7 @@ emit_shadow_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict
                    const int64_t *n_dev, const int64_t *__restrict__ offsets, float lx, float ly,
                    float lz, tm_ray *__restrict__ out, int32_t *__restrict__ src) {
     const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    const HitIn h = load_hit(hits, i, valid_count(n, n_dev));
+    const HitIn h = load_hit(hits, i, valid_count(n, n_dev), mv.nc);
     const int64_t pos = hit_position(h.hit, offsets);
     if (!h.hit) return;
     const int32_t c = h.h1.y;
@@ -245,7 +254,7 @@ emit_specular_kernel(const __grid_constant__ MeshView mv, const tm_ray *__restri
                      const int64_t *__restrict__ offsets, int kind, float ior, float tmax,
                      tm_ray *__restrict__ out, int32_t *__restrict__ src) {
     const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    const HitIn h = load_hit(hits, i, valid_count(n, n_dev));
+    const HitIn h = load_hit(hits, i, valid_count(n, n_dev), mv.nc);
     const int64_t pos = hit_position(h.hit, offsets);
     if (!h.hit) return;
     const int32_t c = h.h1.y;
@@ -300,7 +309,7 @@ namespace {
 // Count, scan and emit with cudaMallocAsync scratch; `emit(nb, offsets)`
 // launches the emit kernel.
 template <class Emit>
-tm_status gen_from_hits(const tm_hit *hits, int64_t n, const int64_t *n_dev, int per_hit,
+tm_status gen_from_hits(const tm_hit *hits, int64_t n, const int64_t *n_dev, int32_t nc, int per_hit,
                         int64_t *count, cudaStream_t s, const char *what, Emit emit) {
     using tmk::kScanBlock;
     if (n == 0) {
@@ -313,7 +322,7 @@ tm_status gen_from_hits(const tm_hit *hits, int64_t n, const int64_t *n_dev, int
     int64_t *offsets = nullptr;
     TM_CUDA(cudaMallocAsync((void **)&counts, sizeof(int32_t) * nb, s));
     TM_CUDA(cudaMallocAsync((void **)&offsets, sizeof(int64_t) * (nb + 1), s));
-    tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, counts);
+    tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, nc, counts);
     tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb, offsets, per_hit, count);
     emit((int)nb, offsets);
     cudaError_t e = cudaGetLastError();
@@ -332,7 +341,7 @@ tm_status gen_from_hits(const tm_hit *hits, int64_t n, const int64_t *n_dev, int
 tm_status launch_gen_shadow(const MeshView &mv, const tm_hit *hits, int64_t n, const int64_t *n_dev,
                             float lx, float ly, float lz, tm_ray *out, int64_t *count, int32_t *src,
                             cudaStream_t s) {
-    return gen_from_hits(hits, n, n_dev, 1, count, s, "gen_shadow launch",
+    return gen_from_hits(hits, n, n_dev, mv.nc, 1, count, s, "gen_shadow launch",
                          [&](int nb, const int64_t *offsets) {
                              tmk::emit_shadow_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
                                  mv, hits, n, n_dev, offsets, lx, ly, lz, out, src);
@@ -342,7 +351,7 @@ tm_status launch_gen_shadow(const MeshView &mv, const tm_hit *hits, int64_t n, c
 tm_status launch_gen_specular(const MeshView &mv, const tm_ray *rays_in, const tm_hit *hits,
                               int64_t n, const int64_t *n_dev, int kind, float ior, float tmax,
                               tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
-    return gen_from_hits(hits, n, n_dev, 1, count, s, "gen_specular launch",
+    return gen_from_hits(hits, n, n_dev, mv.nc, 1, count, s, "gen_specular launch",
                          [&](int nb, const int64_t *offsets) {
                              tmk::emit_specular_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
                                  mv, rays_in, hits, n, n_dev, offsets, kind, ior, tmax, out, src);
@@ -352,7 +361,7 @@ tm_status launch_gen_specular(const MeshView &mv, const tm_ray *rays_in, const t
 tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n,
                                const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                                tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
-    return gen_from_hits(hits, n, n_dev, per_hit, count, s, "gen_secondary launch",
+    return gen_from_hits(hits, n, n_dev, mv.nc, per_hit, count, s, "gen_secondary launch",
                          [&](int nb, const int64_t *offsets) {
                              tmk::emit_secondary_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
                                  mv, hits, n, n_dev, offsets, per_hit, tmax, seed, out, src);
@@ -432,7 +441,7 @@ tm_status launch_gen_secondary_noalloc(const MeshView &mv, const tm_hit *hits, i
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     int32_t *counts = static_cast<int32_t *>(base);
     int64_t *offsets = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(base) + kNoallocCountBytes);
-    tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, counts);
+    tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, mv.nc, counts);
     tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb, offsets, per_hit, count);
     tmk::emit_secondary_kernel<<<(int)nb, kScanBlock, 0, s>>>(mv, hits, n, n_dev, offsets, per_hit,
                                                              tmax, seed, out, src);

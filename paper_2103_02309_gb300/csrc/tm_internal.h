@@ -26,6 +26,7 @@ struct tm_mesh {
     std::vector<int32_t> cold;   // nt*8: V0..V3 (positive orientation), N0..N3 (N_j across V_j)
     std::vector<float> pts4;     // np*4
     std::vector<int32_t> cface;  // nc*8: tri, tet+, tet-, 0, v0, v1, v2, 0
+    std::vector<int32_t> cgeo;   // nc*12: {v0 xyz, tet+}, {v1 xyz, tri}, {v2 xyz, 0} (coordinates as float bits)
     std::vector<int32_t> t20;    // nt*4: VX, N0, N1, N2 (neighbours by rank), when built
     std::vector<int32_t> t20n3;  // nt: N3, when built
     std::vector<int32_t> t20aos; // nt*5: VX, N0..N3 at a 20-byte stride, when built
@@ -40,6 +41,7 @@ struct tm_mesh {
     float4 *d_pts = nullptr;
     int4 *d_cold = nullptr;
     int4 *d_cface = nullptr;
+    int4 *d_cgeo = nullptr;
     int32_t *d_seeds = nullptr;  // located tets of a kSeedGrid^3 lattice over the bounding box
     int4 *d_t20 = nullptr;
     int32_t *d_t20n3 = nullptr;
@@ -60,6 +62,7 @@ struct MeshView {
     const float4 *pts;
     const int4 *cold;
     const int4 *cface;
+    const int4 *cgeo;      // three int4 per triangle: its vertices' coordinates and tet+ (hit geometry)
     int32_t nt, np, nc;
     float extent;
     const int32_t *seeds;  // kSeedGrid^3 source tets for point location (may be null)
@@ -77,6 +80,7 @@ inline MeshView mesh_view(const tm_mesh *m) {
     v.pts = m->d_pts;
     v.cold = m->d_cold;
     v.cface = m->d_cface;
+    v.cgeo = m->d_cgeo;
     v.nt = (int32_t)m->nt;
     v.np = (int32_t)m->np;
     v.nc = (int32_t)m->nc;

@@ -233,12 +233,13 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
 // instead of two, with some spill on its rare paths, and measured 20 %
 // faster on bounce and ambient-occlusion rays.  (The double-precision arm,
 // whose state is twice as wide, keeps its registers.)  The finish phase
-// gained nothing from the same change.
+// keeps four blocks an SM at 64 registers as well, which it fits without
+// spilling.
 #ifndef TM_START_MIN_BLOCKS
 #define TM_START_MIN_BLOCKS 4
 #endif
 #ifndef TM_FINISH_MIN_BLOCKS
-#define TM_FINISH_MIN_BLOCKS 1
+#define TM_FINISH_MIN_BLOCKS 4
 #endif
 
 template <int MODE, bool MULTI>
@@ -265,9 +266,13 @@ start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
 // float32 t could be off by more than about 2e-6 relative.
 constexpr float kFinalCond = 32.f;
 
-// Phase 3 for one ray: the hit (or miss) from the end record.
+// Phase 3 for one ray: the hit (or miss) from the end record.  In guard
+// mode with `defer`, a hit whose float32 test is ill-conditioned is left
+// untouched and reported (returns true), for a second call with `direct64`
+// that goes straight to double precision.
 template <int MODE>
-__device__ __forceinline__ void finish_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp) {
+__device__ __forceinline__ bool finish_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
+                                           bool defer = false, bool direct64 = false) {
     const int4 e0 = __ldcs(reinterpret_cast<const int4 *>(hp));
     const int4 e1 = __ldcs(reinterpret_cast<const int4 *>(hp) + 1);
     const int32_t tet = e0.y;
@@ -288,18 +293,22 @@ __device__ __forceinline__ void finish_one(const MeshView &mv, const tm_ray *rp,
         const float4 w0 = __ldg(reinterpret_cast<const float4 *>(rp));
         const float4 w1 = __ldg(reinterpret_cast<const float4 *>(rp) + 1);
         const int32_t c = (int32_t)(code & ~TM_CFACE_FLAG);
-        const int4 r0 = __ldg(mv.cface + 2 * c);
-        const int4 r1 = __ldg(mv.cface + 2 * c + 1);  // vertex ids validated by the host build
-        const float4 a = __ldg(mv.pts + r1.x), b = __ldg(mv.pts + r1.y), d = __ldg(mv.pts + r1.z);
+        // the triangle's vertices inline: {a, tet+}, {b, tri}, {d, 0}
+        const int4 g0 = __ldg(mv.cgeo + 3 * c), g1 = __ldg(mv.cgeo + 3 * c + 1),
+                   g2 = __ldg(mv.cgeo + 3 * c + 2);
+        const float4 a = make_float4(__int_as_float(g0.x), __int_as_float(g0.y), __int_as_float(g0.z), 0.f);
+        const float4 b = make_float4(__int_as_float(g1.x), __int_as_float(g1.y), __int_as_float(g1.z), 0.f);
+        const float4 d = make_float4(__int_as_float(g2.x), __int_as_float(g2.y), __int_as_float(g2.z), 0.f);
         float th, u, v;
         if (MODE == FP64) {
             double td, ud, vd, cd;
             mt_hit<double>(w0, w1, a, b, d, td, ud, vd, cd);
             th = (float)td; u = (float)ud; v = (float)vd;
         } else {
-            float cond;
-            mt_hit<float>(w0, w1, a, b, d, th, u, v, cond);
-            if (MODE == FP32G && !(cond <= kFinalCond)) {
+            float cond = 0.f;
+            if (!(MODE == FP32G && direct64)) mt_hit<float>(w0, w1, a, b, d, th, u, v, cond);
+            if (MODE == FP32G && (direct64 || !(cond <= kFinalCond))) {
+                if (defer) return true;
                 double td, ud, vd, cd;
                 mt_hit<double>(w0, w1, a, b, d, td, ud, vd, cd);
                 th = (float)td; u = (float)ud; v = (float)vd;
@@ -307,34 +316,67 @@ __device__ __forceinline__ void finish_one(const MeshView &mv, const tm_ray *rp,
             }
         }
         if (th <= w1.w) {
-            tri = r0.x;
+            tri = g1.w;
             cf = c;
             t = th;
             b1 = u;
             b2 = v;
-            if (r0.y != tet) flags |= TM_HIT_SIDE_NEG;
+            if (g0.w != tet) flags |= TM_HIT_SIDE_NEG;
         }
     }
     __stcs(reinterpret_cast<int4 *>(hp), make_int4(tri, __float_as_int(t), __float_as_int(b1),
                                                    __float_as_int(b2)));
     __stcs(reinterpret_cast<int4 *>(hp) + 1, make_int4(tet, cf, (int)steps, (int)flags));
+    return false;
 }
 
 template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, TM_FINISH_MIN_BLOCKS)
+__device__ __forceinline__ bool finish_at(const MeshView &mv0, const tm_ray *rays0, tm_hit *hits0,
+                                          const BatchDesc *descs, int n_meshes, int64_t r,
+                                          bool defer, bool direct64) {
+    if (MULTI) {
+        const Slot s = find_slot(descs, n_meshes, (unsigned long long)r);
+        const BatchDesc &D = descs[s.m];
+        return finish_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, defer, direct64);
+    }
+    return finish_one<MODE>(mv0, rays0 + r, hits0 + r, defer, direct64);
+}
+
+constexpr int kFinishBlock = 256;
+
+// In guard mode about one hit in twenty needs the double-precision test,
+// and on GB300's narrow FP64 pipe a warp pays for it if any of its lanes
+// does.  So each block first finishes its 256 rays in float32, queues the
+// ill-conditioned ones in shared memory, then redoes those packed into the
+// block's first lanes: about one warp of double-precision work per 256
+// rays instead of six.
+template <int MODE, bool MULTI>
+__global__ void __launch_bounds__(kFinishBlock, MODE == FP64 ? 1 : TM_FINISH_MIN_BLOCKS)
 finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
               tm_hit *__restrict__ hits0, const BatchDesc *__restrict__ descs, int n_meshes,
               const __grid_constant__ PhaseParams P) {
     const int64_t n = ray_count(P);
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        if (MULTI) {
-            const Slot s = find_slot(descs, n_meshes, (unsigned long long)r);
-            const BatchDesc &D = descs[s.m];
-            finish_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local);
-        } else {
-            finish_one<MODE>(mv0, rays0 + r, hits0 + r);
+    if constexpr (MODE == FP32G) {
+        __shared__ int queue[kFinishBlock];
+        __shared__ int queued;
+        // block-uniform trip count: every thread reaches every barrier
+        for (int64_t base = blockIdx.x * (int64_t)kFinishBlock; base < n;
+             base += (int64_t)gridDim.x * kFinishBlock) {
+            if (threadIdx.x == 0) queued = 0;
+            __syncthreads();
+            const int64_t r = base + threadIdx.x;
+            if (r < n && finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, r, true, false))
+                queue[atomicAdd(&queued, 1)] = (int)threadIdx.x;
+            __syncthreads();
+            if ((int)threadIdx.x < queued)
+                finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, base + queue[threadIdx.x],
+                                       false, true);
+            __syncthreads();
         }
+    } else {
+        for (int64_t r = blockIdx.x * (int64_t)kFinishBlock + threadIdx.x; r < n;
+             r += (int64_t)gridDim.x * kFinishBlock)
+            finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, r, false, false);
     }
 }
 
@@ -1059,7 +1101,7 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     walk_kernel<MODE, FMT, BOUNDED, MULTI><<<walk_grid, block, smem, s>>>(mv, rays, hits, descs,
                                                                            n_meshes, W);
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
-    finish_kernel<MODE, MULTI><<<(int)g, 256, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
+    finish_kernel<MODE, MULTI><<<(int)g, kFinishBlock, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }

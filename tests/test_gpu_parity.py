@@ -396,6 +396,22 @@ def test_edge_cases(tmx, tiny):
     m.trace(rays, hits=hits, n_dev=torch.tensor([100], dtype=torch.int64, device="cuda"))
     h = hits.cpu().numpy()
     assert (h[100:] == -7).all() and (h[:100, 6] != -7).all()
+    # hits on faces this mesh does not have (a foreign or corrupted hit buffer)
+    # generate no rays: the generators treat them as misses
+    g = m.trace(rays)
+    good = g.clone()
+    n_hit = int((tmx.unpack_hits(good)["tri"] >= 0).sum())
+    assert n_hit > 10
+    bad = g.clone()
+    hit_rows = torch.nonzero(bad[:, 0] >= 0).flatten()
+    bad[hit_rows[:5], 5] = tiny.s.n_tris + 3
+    bad[hit_rows[5:10], 5] = -2
+    for gen in (lambda hh: m.gen_secondary(hh, 2, np.inf, seed=3),
+                lambda hh: m.gen_shadow(hh, (0.5, 0.9, 0.5)),
+                lambda hh: m.gen_specular(rays, hh, "reflect", 1.5)):
+        _, cnt_good, _ = gen(good)
+        _, cnt_bad, _ = gen(bad)
+        assert int(cnt_good.item()) - int(cnt_bad.item()) == 10 * (int(cnt_good.item()) // n_hit)
 
 
 def test_axis_aligned_rays_on_unjittered_grid(tmx):
