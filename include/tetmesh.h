@@ -256,7 +256,7 @@ tm_status tm_map_ids(const tm_mesh *mesh, int kind, int direction, const int32_t
  * int32 [n]), or -1 when q[i] is outside the mesh or the walk exceeds its
  * bound.  hint (DEVICE int32 [n], may be NULL) gives a per-point source tet;
  * otherwise `source` (an internal id), or with source = -1 the located tet of
- * the nearest point of a 16^3 lattice over the bounding box (located once
+ * the nearest point of a 32^3 lattice over the bounding box (located once
  * when the mesh is uploaded), so that walks stay short. */
 tm_status tm_locate(const tm_mesh *mesh, const float *q, int64_t n, const int32_t *hint,
                     int32_t source, int32_t *tet_out, void *stream);

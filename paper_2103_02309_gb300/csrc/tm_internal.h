@@ -54,7 +54,7 @@ struct tm_mesh {
 
 // Point location starts from the located tet of the nearest lattice point
 // (a coarse grid of precomputed source tets) instead of one fixed source.
-constexpr int kSeedGrid = 16;
+constexpr int kSeedGrid = 32;
 
 // What a kernel needs to walk one mesh.
 struct MeshView {

@@ -343,13 +343,17 @@ __device__ __forceinline__ bool finish_at(const MeshView &mv0, const tm_ray *ray
 }
 
 constexpr int kFinishBlock = 256;
+#ifndef TM_FINISH_RAYS_PER_THREAD
+#define TM_FINISH_RAYS_PER_THREAD 4
+#endif
+constexpr int kFinishChunk = kFinishBlock * TM_FINISH_RAYS_PER_THREAD;
 
 // In guard mode about one hit in twenty needs the double-precision test,
 // and on GB300's narrow FP64 pipe a warp pays for it if any of its lanes
-// does.  So each block first finishes its 256 rays in float32, queues the
-// ill-conditioned ones in shared memory, then redoes those packed into the
-// block's first lanes: about one warp of double-precision work per 256
-// rays instead of six.
+// does.  So each block first finishes a chunk of rays in float32 (four a
+// thread), queues the ill-conditioned ones in shared memory, then redoes
+// those packed into full warps: about two warps of double-precision work
+// per 1024 rays instead of some 25.
 template <int MODE, bool MULTI>
 __global__ void __launch_bounds__(kFinishBlock, MODE == FP64 ? 1 : TM_FINISH_MIN_BLOCKS)
 finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ rays0,
@@ -357,20 +361,21 @@ finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ r
               const __grid_constant__ PhaseParams P) {
     const int64_t n = ray_count(P);
     if constexpr (MODE == FP32G) {
-        __shared__ int queue[kFinishBlock];
+        __shared__ int queue[kFinishChunk];
         __shared__ int queued;
         // block-uniform trip count: every thread reaches every barrier
-        for (int64_t base = blockIdx.x * (int64_t)kFinishBlock; base < n;
-             base += (int64_t)gridDim.x * kFinishBlock) {
+        for (int64_t base = blockIdx.x * (int64_t)kFinishChunk; base < n;
+             base += (int64_t)gridDim.x * kFinishChunk) {
             if (threadIdx.x == 0) queued = 0;
             __syncthreads();
-            const int64_t r = base + threadIdx.x;
-            if (r < n && finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, r, true, false))
-                queue[atomicAdd(&queued, 1)] = (int)threadIdx.x;
+            for (int j = threadIdx.x; j < kFinishChunk; j += kFinishBlock) {
+                const int64_t r = base + j;
+                if (r < n && finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, r, true, false))
+                    queue[atomicAdd(&queued, 1)] = j;
+            }
             __syncthreads();
-            if ((int)threadIdx.x < queued)
-                finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, base + queue[threadIdx.x],
-                                       false, true);
+            for (int q = threadIdx.x; q < queued; q += kFinishBlock)
+                finish_at<MODE, MULTI>(mv0, rays0, hits0, descs, n_meshes, base + queue[q], false, true);
             __syncthreads();
         }
     } else {
@@ -1101,7 +1106,9 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     walk_kernel<MODE, FMT, BOUNDED, MULTI><<<walk_grid, block, smem, s>>>(mv, rays, hits, descs,
                                                                            n_meshes, W);
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
-    finish_kernel<MODE, MULTI><<<(int)g, kFinishBlock, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
+    int64_t gf = g;
+    if (MODE == FP32G) gf = std::min<int64_t>((W.n_cap + kFinishChunk - 1) / kFinishChunk, gmax);
+    finish_kernel<MODE, MULTI><<<(int)gf, kFinishBlock, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
