@@ -268,6 +268,25 @@ def test_hilbert_and_other_orders_identical(tmx, other):
     assert np.array_equal(a.tperm[ga["tet"]][~tie], b.tperm[gb["tet"]][~tie])
 
 
+def test_medium_full_size_orders_and_oracle(tmx):
+    """The medium workload at full size (64^3 cells, 1.57 M tets, 1920x1080
+    camera rays): Hilbert and input order give identical hits on every ray,
+    and sampled rays equal the oracle's."""
+    c = camera_case(tmx, "medium")
+    b = Case(tmx, c.s, "input")
+    o, d = sg.camera_rays(c.s.camera)
+    assert len(o) == 1920 * 1080
+    ga = c.gpu_trace(tmx, o, d, np.inf, c.cam_internal)
+    gb = b.gpu_trace(tmx, o, d, np.inf, b.tinv[c.cam_in[0]])
+    tie = ((ga["flags"] | gb["flags"]) & tmx.HIT_TIE) != 0
+    assert tie.mean() < 1e-3
+    for k in ("tri", "t", "b1", "b2", "steps"):
+        assert np.array_equal(ga[k][~tie], gb[k][~tie]), k
+    sel = np.random.default_rng(9).choice(len(o), 20000, replace=False)
+    w = c.oracle_trace(o[sel], d[sel], np.inf, c.cam_in[0])
+    compare(c.s.points, c.s.tris, {k: v[sel] for k, v in ga.items()}, w)
+
+
 @pytest.fixture(scope="module")
 def precision(tmx):
     """The full-size precision workload (128^3 cells, 2048x2048 camera rays)."""
