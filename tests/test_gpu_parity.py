@@ -433,6 +433,34 @@ def test_edge_cases(tmx, tiny):
         assert int(cnt_good.item()) - int(cnt_bad.item()) == 10 * (int(cnt_good.item()) // n_hit)
 
 
+def test_grazing_hits_queue_for_the_final_fp64_test(tmx):
+    """Rays grazing a jittered plane of triangles: most hits are
+    ill-conditioned, so the finish phase queues hundreds of rays per chunk for
+    its double-precision test.  Hits still equal the oracle's, and guard mode
+    marks the re-tested ones."""
+    n, layer = 8, 5
+    pts, tets = sg.freudenthal_grid(n, 0.15, 11)
+    tris = sg.constrained_faces(n, sg.slab_cells(n, layer))
+    c = Case(tmx, sg.Scene("slab", n, 0.15, 11, pts, tets, tris, None))
+    g = np.random.default_rng(5)
+    cnt = 6000
+    o = np.stack([g.uniform(0.05, 0.3, cnt), g.uniform(0.1, 0.9, cnt), g.uniform(0.55, 0.6, cnt)],
+                 1).astype(np.float32)
+    th = g.uniform(-0.3, 0.3, cnt)
+    d = np.stack([np.cos(th), np.sin(th), g.uniform(0.03, 0.08, cnt)], 1)
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    start, mb = c.om.locate(o)
+    keep = mb > 1e-9
+    o, d, start = o[keep], d[keep], start[keep]
+    w = c.oracle_trace(o, d, np.inf, start)
+    assert (w["tri"] >= 0).mean() > 0.3
+    for mode in ("fp64", "fp32g"):
+        gh = c.gpu_trace(tmx, o, d, np.inf, c.tinv[start], mode=mode)
+        compare(c.s.points, c.s.tris, gh, w)
+    hit = gh["tri"] >= 0
+    assert ((gh["flags"][hit] & tmx.HIT_FINAL_FP64) != 0).mean() > 0.3
+
+
 def test_axis_aligned_rays_on_unjittered_grid(tmx):
     """Rays through grid vertices and edges: exact zeros are broken by ids, walks end."""
     n = 6
