@@ -29,8 +29,13 @@
 //     out-of-line call; the walks over the paper's records park the ray in
 //     its hit slot and re-decide the step at the lane's next refill, with no
 //     walk state live across that call.
+//     Bounded walks (short rays) also prefetch into L2, at each refill, the
+//     records of the rays a little further along the cursor.
 //  3. finish_kernel, one thread per ray: the ray-triangle test on the hit
-//     triangle in its own vertex order, with the FP64 guard, into the hit.
+//     triangle in its own vertex order (vertices read inline with the
+//     triangle), with the FP64 guard, into the hit.  In guard mode a block
+//     queues its ill-conditioned hits and redoes them in double precision
+//     packed into full warps.
 //
 // Keeping the once-per-ray work out of the walk kernel keeps the walk's
 // register state small and its code free of calls except the rare FP64
