@@ -593,7 +593,12 @@ tm_status tm_upload(tm_mesh *m) {
     float *d_q = nullptr;
     TM_CUDA(cudaMalloc(&m->d_seeds, sizeof(int32_t) * ns));
     TM_CUDA(cudaMalloc(&d_q, sizeof(float) * 3 * ns));
-    TM_CUDA(cudaMemcpy(d_q, q.data(), sizeof(float) * 3 * ns, cudaMemcpyHostToDevice));
+    const cudaError_t ec = cudaMemcpy(d_q, q.data(), sizeof(float) * 3 * ns, cudaMemcpyHostToDevice);
+    if (ec != cudaSuccess) {
+        cudaFree(d_q);
+        tm_set_error("cudaMemcpy (seed lattice)", ec);
+        return TM_ERR_CUDA;
+    }
     MeshView mv = mesh_view(m);
     mv.seeds = nullptr;  // the lattice itself is located from the default source
     const uint32_t bound = (uint32_t)(64.0 * std::cbrt((double)m->nt) * 8.0 + 1024.0);

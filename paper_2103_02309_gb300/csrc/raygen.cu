@@ -321,7 +321,12 @@ tm_status gen_from_hits(const tm_hit *hits, int64_t n, const int64_t *n_dev, int
     int32_t *counts = nullptr;
     int64_t *offsets = nullptr;
     TM_CUDA(cudaMallocAsync((void **)&counts, sizeof(int32_t) * nb, s));
-    TM_CUDA(cudaMallocAsync((void **)&offsets, sizeof(int64_t) * (nb + 1), s));
+    cudaError_t ea = cudaMallocAsync((void **)&offsets, sizeof(int64_t) * (nb + 1), s);
+    if (ea != cudaSuccess) {
+        cudaFreeAsync(counts, s);
+        tm_set_error("cudaMallocAsync (scan offsets)", ea);
+        return TM_ERR_CUDA;
+    }
     tmk::count_hits_kernel<<<(int)nb, kScanBlock, 0, s>>>(hits, n, n_dev, nc, counts);
     tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb, offsets, per_hit, count);
     emit((int)nb, offsets);

@@ -1231,7 +1231,12 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
     if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
     unsigned long long *cursor = nullptr;  // the walk's ray counter
     TM_CUDA(cudaMallocAsync((void **)&cursor, sizeof(unsigned long long), s));
-    TM_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
+    const cudaError_t ez = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s);
+    if (ez != cudaSuccess) {
+        cudaFreeAsync(cursor, s);
+        tm_set_error("cudaMemsetAsync (ray cursor)", ez);
+        return TM_ERR_CUDA;
+    }
     WalkParams W;
     W.n_cap = n;
     W.n_dev = n_dev;
