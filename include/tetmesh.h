@@ -242,6 +242,14 @@ tm_status tm_mesh_export_faces(const tm_mesh *mesh, int32_t *faces);
 /* The same for the 16-byte entries: faces16 int32[n_tets*16]. */
 tm_status tm_mesh_export_faces16(const tm_mesh *mesh, int32_t *faces16);
 
+/* Copies the restart records into a HOST buffer int32[n_tris*2*24]: for side
+ * s of triangle c (record 2c + s, the index a restart ray's start field
+ * names, Sec. 6) the tet on that side, {V0..V3}, {N0..N3} (its cold record),
+ * the positions of V0..V3 (12 float32 bit patterns), then {T, skip, 0, 0}
+ * with skip the local index of the face it shares with c; T = skip = -1 on a
+ * side with no tet.  Always built. */
+tm_status tm_mesh_export_restart(const tm_mesh *mesh, int32_t *restart);
+
 enum { TM_IDS_TET = 0, TM_IDS_POINT = 1 };
 enum { TM_TO_INPUT = 0, TM_TO_INTERNAL = 1 };
 /* Converts n ids (HOST arrays) between internal and input numbering.  Ids

@@ -77,6 +77,7 @@ _SIGS = {
     "tm_mesh_export_tet20": ([P, P, P, P], ctypes.c_int),
     "tm_mesh_export_faces": ([P, P], ctypes.c_int),
     "tm_mesh_export_faces16": ([P, P], ctypes.c_int),
+    "tm_mesh_export_restart": ([P, P], ctypes.c_int),
     "tm_read_probe": ([P, i64, ctypes.c_int, P, P], ctypes.c_int),
     "tm_map_ids": ([P, ctypes.c_int, ctypes.c_int, P, P, i64], ctypes.c_int),
     "tm_hilbert_keys": ([P, i64, ctypes.c_int, P], ctypes.c_int),

@@ -504,6 +504,32 @@ tm_status tm_build_host(const float *points, int64_t np, const int32_t *tets_in,
         g[7] = (int32_t)c;
         g[11] = 0;
     }
+    // restart records: for side s of triangle c, the tet on that side (its
+    // cold record, its vertices' positions, and the local index of the face
+    // it shares with c), so that a restarted ray needs one read to start
+    m->restart.assign((size_t)nc * 2 * 24, 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int side = 0; side < 2; ++side) {
+            int32_t *r = &m->restart[24 * (2 * c + side)];
+            const int32_t T = m->cface[8 * c + 1 + side];
+            r[20] = -1;
+            r[21] = -1;
+            if (T < 0) continue;
+            const int32_t *V = &m->cold[8 * (int64_t)T];
+            const int32_t *N = &m->cold[8 * (int64_t)T + 4];
+            int skip = -1;
+            for (int k = 0; k < 4; ++k)
+                if ((uint32_t)N[k] == (TM_CFACE_FLAG | (uint32_t)c)) skip = k;
+            for (int k = 0; k < 4; ++k) {
+                r[k] = V[k];
+                r[4 + k] = N[k];
+                std::memcpy(&r[8 + 3 * k], &m->pts4[4 * (int64_t)V[k]], 3 * sizeof(float));
+            }
+            r[20] = T;
+            r[21] = skip;
+        }
+    }
 
     // default locate source: the tet whose centroid is nearest the box centre
     const double cen[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
@@ -536,13 +562,15 @@ tm_status tm_upload(tm_mesh *m) {
     const size_t b_tet = sizeof(int4) * (size_t)m->nt, b_pts = sizeof(float4) * (size_t)m->np,
                  b_cold = 2 * sizeof(int4) * (size_t)m->nt,
                  b_cf = 2 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1),
-                 b_cg = 3 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1);
+                 b_cg = 3 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1),
+                 b_rs = 12 * sizeof(int4) * (size_t)(m->nc > 0 ? m->nc : 1);
     cudaError_t e;
     if ((e = cudaMalloc(&m->d_tet16, b_tet)) != cudaSuccess ||
         (e = cudaMalloc(&m->d_pts, b_pts)) != cudaSuccess ||
         (e = cudaMalloc(&m->d_cold, b_cold)) != cudaSuccess ||
         (e = cudaMalloc(&m->d_cface, b_cf)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_cgeo, b_cg)) != cudaSuccess) {
+        (e = cudaMalloc(&m->d_cgeo, b_cg)) != cudaSuccess ||
+        (e = cudaMalloc(&m->d_restart, b_rs)) != cudaSuccess) {
         tm_set_error("cudaMalloc", e);
         return e == cudaErrorMemoryAllocation ? TM_ERR_OOM : TM_ERR_CUDA;
     }
@@ -552,10 +580,13 @@ tm_status tm_upload(tm_mesh *m) {
     if (m->nc > 0)
         TM_CUDA(cudaMemcpy(m->d_cface, m->cface.data(), 2 * sizeof(int4) * (size_t)m->nc,
                            cudaMemcpyHostToDevice));
-    if (m->nc > 0)
+    if (m->nc > 0) {
         TM_CUDA(cudaMemcpy(m->d_cgeo, m->cgeo.data(), 3 * sizeof(int4) * (size_t)m->nc,
                            cudaMemcpyHostToDevice));
-    m->device_bytes = (int64_t)(b_tet + b_pts + b_cold + b_cf + b_cg);
+        TM_CUDA(cudaMemcpy(m->d_restart, m->restart.data(), 12 * sizeof(int4) * (size_t)m->nc,
+                           cudaMemcpyHostToDevice));
+    }
+    m->device_bytes = (int64_t)(b_tet + b_pts + b_cold + b_cf + b_cg + b_rs);
     if (!m->t20.empty()) {
         TM_CUDA(cudaMalloc(&m->d_t20, sizeof(int4) * (size_t)m->nt));
         TM_CUDA(cudaMalloc(&m->d_t20n3, sizeof(int32_t) * (size_t)m->nt));
@@ -626,6 +657,8 @@ void tm_free_device(tm_mesh *m) {
     cudaFree(m->d_cface);
     cudaFree(m->d_cgeo);
     m->d_cgeo = nullptr;
+    cudaFree(m->d_restart);
+    m->d_restart = nullptr;
     cudaFree(m->d_seeds);
     m->d_seeds = nullptr;
     cudaFree(m->d_t20);

@@ -140,6 +140,12 @@ tm_status tm_mesh_export_faces16(const tm_mesh *m, int32_t *faces16) {
     return TM_OK;
 }
 
+tm_status tm_mesh_export_restart(const tm_mesh *m, int32_t *restart) {
+    if (!m || !restart) return TM_ERR_ARG;
+    std::memcpy(restart, m->restart.data(), sizeof(int32_t) * m->restart.size());
+    return TM_OK;
+}
+
 tm_status tm_map_ids(const tm_mesh *m, int kind, int direction, const int32_t *in, int32_t *out,
                      int64_t n) {
     if (!m || (n > 0 && (!in || !out)) || n < 0) return TM_ERR_ARG;

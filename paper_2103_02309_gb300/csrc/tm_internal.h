@@ -27,6 +27,7 @@ struct tm_mesh {
     std::vector<float> pts4;     // np*4
     std::vector<int32_t> cface;  // nc*8: tri, tet+, tet-, 0, v0, v1, v2, 0
     std::vector<int32_t> cgeo;   // nc*12: {v0 xyz, tet+}, {v1 xyz, tri}, {v2 xyz, 0} (coordinates as float bits)
+    std::vector<int32_t> restart; // nc*2*24: per triangle side, the tet there: V, N, vertex xyz, {T, skip}
     std::vector<int32_t> t20;    // nt*4: VX, N0, N1, N2 (neighbours by rank), when built
     std::vector<int32_t> t20n3;  // nt: N3, when built
     std::vector<int32_t> t20aos; // nt*5: VX, N0..N3 at a 20-byte stride, when built
@@ -42,6 +43,7 @@ struct tm_mesh {
     int4 *d_cold = nullptr;
     int4 *d_cface = nullptr;
     int4 *d_cgeo = nullptr;
+    int4 *d_restart = nullptr;
     int32_t *d_seeds = nullptr;  // located tets of a kSeedGrid^3 lattice over the bounding box
     int4 *d_t20 = nullptr;
     int32_t *d_t20n3 = nullptr;
@@ -63,6 +65,7 @@ struct MeshView {
     const int4 *cold;
     const int4 *cface;
     const int4 *cgeo;      // three int4 per triangle: its vertices' coordinates and tet+ (hit geometry)
+    const int4 *restart;   // six int4 per triangle side: the restart tet, inline (restarted rays)
     int32_t nt, np, nc;
     float extent;
     const int32_t *seeds;  // kSeedGrid^3 source tets for point location (may be null)
@@ -81,6 +84,7 @@ inline MeshView mesh_view(const tm_mesh *m) {
     v.cold = m->d_cold;
     v.cface = m->d_cface;
     v.cgeo = m->d_cgeo;
+    v.restart = m->d_restart;
     v.nt = (int32_t)m->nt;
     v.np = (int32_t)m->np;
     v.nc = (int32_t)m->nc;

@@ -186,18 +186,12 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
     } else {
         const int32_t code = -1 - start;
         const int32_t c = code >> 1;
-        if (c < mv.nc) {
-            const int4 r0 = __ldg(mv.cface + 2 * c);
-            T = (code & 1) ? r0.z : r0.y;
-        }
-        if (T >= mv.nt) T = -1;
+        int skip = -1;
+        // the tet on the restart side, its entry face and its vertices, from
+        // the side's restart record
+        if (c < mv.nc) ok = restart_init<MODE>(mv, B, (int64_t)code, T, skip, sc, S, next);
         if (T >= 0) {
-            const int4 cn = __ldg(mv.cold + 2 * T + 1);
-            const uint32_t want = TM_CFACE_FLAG | (uint32_t)c;
-            int skip = (uint32_t)cn.x == want ? 0 : (uint32_t)cn.y == want ? 1
-                     : (uint32_t)cn.z == want ? 2 : (uint32_t)cn.w == want ? 3 : -1;
             if (skip >= 0) {
-                ok = line_init<MODE>(mv, B, T, skip, sc, S, next);
                 for (int it = 0; !ok && it < 16; ++it) {
                     // the line misses T by rounding: one 3-D step, then retry
                     sc.flags |= TM_HIT_RESTART_3D;

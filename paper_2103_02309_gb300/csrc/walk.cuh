@@ -204,18 +204,13 @@ template <class R> struct WalkState {
 // and returns the raw neighbour value across it; returns false when no
 // face or more than one face qualifies.
 template <int MODE, class R>
-__device__ __forceinline__ bool line_init(const MeshView &mv, const Basis<R> &B, int32_t T, int skip,
-                                          SignCtx &c, WalkState<R> &S, uint32_t &next) {
-    const int4 cv = __ldg(mv.cold + 2 * T);
-    const int4 cn = __ldg(mv.cold + 2 * T + 1);
-    const int32_t V[4] = {cv.x, cv.y, cv.z, cv.w};
-    const uint32_t NB[4] = {(uint32_t)cn.x, (uint32_t)cn.y, (uint32_t)cn.z, (uint32_t)cn.w};
+__device__ __forceinline__ bool line_init_core(const Basis<R> &B, int32_t T, int skip,
+                                               const int32_t (&V)[4], const uint32_t (&NB)[4],
+                                               const float (&X)[4][3], SignCtx &c, WalkState<R> &S,
+                                               uint32_t &next) {
     P2<R> P[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float4 x = __ldg(mv.pts + V[k]);
-        P[k] = B.project(x.x, x.y, x.z);
-    }
+    for (int k = 0; k < 4; ++k) P[k] = B.project(X[k][0], X[k][1], X[k][2]);
     int found = -1, count = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -245,6 +240,50 @@ __device__ __forceinline__ bool line_init(const MeshView &mv, const Basis<R> &B,
     S.m1 = guard_mag(S.p1, c.tau);
     S.m2 = guard_mag(S.p2, c.tau);
     return true;
+}
+
+// line_init_core on tet T read from its cold record and the points.
+template <int MODE, class R>
+__device__ __forceinline__ bool line_init(const MeshView &mv, const Basis<R> &B, int32_t T, int skip,
+                                          SignCtx &c, WalkState<R> &S, uint32_t &next) {
+    const int4 cv = __ldg(mv.cold + 2 * T);
+    const int4 cn = __ldg(mv.cold + 2 * T + 1);
+    const int32_t V[4] = {cv.x, cv.y, cv.z, cv.w};
+    const uint32_t NB[4] = {(uint32_t)cn.x, (uint32_t)cn.y, (uint32_t)cn.z, (uint32_t)cn.w};
+    float X[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 x = __ldg(mv.pts + V[k]);
+        X[k][0] = x.x; X[k][1] = x.y; X[k][2] = x.z;
+    }
+    return line_init_core<MODE>(B, T, skip, V, NB, X, c, S, next);
+}
+
+// line_init_core on the restart record of triangle side (2c + side): the
+// tet on that side with its ids, neighbours and vertex positions inline, so
+// a restarted ray reaches its line test after one read.  Six int4:
+// {V0..V3}, {N0..N3}, {x0 y0 z0 x1}, {y1 z1 x2 y2}, {z2 x3 y3 z3}, {T, skip, 0, 0}.
+// Returns false with T = -1 when the side has no tet.
+template <int MODE, class R>
+__device__ __forceinline__ bool restart_init(const MeshView &mv, const Basis<R> &B, int64_t rec,
+                                             int32_t &T, int &skip, SignCtx &c, WalkState<R> &S,
+                                             uint32_t &next) {
+    const int4 *r = mv.restart + 6 * rec;
+    const int4 cv = __ldg(r), cn = __ldg(r + 1), g0 = __ldg(r + 2), g1 = __ldg(r + 3),
+               g2 = __ldg(r + 4), h = __ldg(r + 5);
+    T = h.x;
+    skip = h.y;
+    if (T < 0 || T >= mv.nt || skip < 0 || skip > 3) {
+        T = -1;
+        return false;
+    }
+    const int32_t V[4] = {cv.x, cv.y, cv.z, cv.w};
+    const uint32_t NB[4] = {(uint32_t)cn.x, (uint32_t)cn.y, (uint32_t)cn.z, (uint32_t)cn.w};
+    const float X[4][3] = {{__int_as_float(g0.x), __int_as_float(g0.y), __int_as_float(g0.z)},
+                           {__int_as_float(g0.w), __int_as_float(g1.x), __int_as_float(g1.y)},
+                           {__int_as_float(g1.z), __int_as_float(g1.w), __int_as_float(g2.x)},
+                           {__int_as_float(g2.y), __int_as_float(g2.z), __int_as_float(g2.w)}};
+    return line_init_core<MODE>(B, T, skip, V, NB, X, c, S, next);
 }
 
 // The rare restart fallback: one 3-D face-plane step in double precision

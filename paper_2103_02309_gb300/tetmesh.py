@@ -187,6 +187,12 @@ class Mesh:
         N.check(N.lib.tm_mesh_export_faces16(self._h, _hptr(f)), "tm_mesh_export_faces16")
         return f
 
+    def export_restart(self) -> np.ndarray:
+        """Restart records int32 [n_tris, 2, 24] (see tm_mesh_export_restart)."""
+        r = np.empty((max(self.info.n_tris, 0), 2, 24), np.int32)
+        N.check(N.lib.tm_mesh_export_restart(self._h, _hptr(r)), "tm_mesh_export_restart")
+        return r
+
     def map_ids(self, kind, direction, ids) -> np.ndarray:
         a = np.ascontiguousarray(ids, np.int32).reshape(-1)
         out = np.empty_like(a)

@@ -257,3 +257,31 @@ def test_face16_entries(tmx):
             assert g & 0x1FFFFFFF == n and g >> 31 == 0
             assert (g >> 29) & 3 == int((V[n] < w).sum())
             assert np.array_equal(G[t, r, 1:4], F[t, r, 2:5])
+
+
+def test_restart_records(tmx):
+    """Restart record of side s of triangle c: the tet the oracle's adjacency
+    puts on that side, whose face opposite V[skip] is the triangle, with its
+    cold record and its vertices' input positions inline."""
+    s = sg.make_config("tiny")
+    m = tmx.Mesh(s.points, s.tets, s.tris, upload=False)
+    e = m.export()
+    R = m.export_restart()
+    _, _, ctet = oracle.OracleMesh(s.points, s.tets, s.tris).arrays()
+    pperm, tperm = e["point_perm"], e["tet_perm"]
+    assert R.shape == (len(s.tris), 2, 24)
+    for c in range(len(s.tris)):
+        tri = set(int(v) for v in s.tris[c])
+        for side in range(2):
+            r = R[c, side]
+            T, skip = int(r[20]), int(r[21])
+            if ctet[c, side] < 0:
+                assert T == -1 and skip == -1
+                continue
+            assert tperm[T] == ctet[c, side]
+            assert np.array_equal(r[0:8], e["cold"][T])
+            V = r[0:4]
+            assert set(int(pperm[V[k]]) for k in range(4) if k != skip) == tri
+            xyz = r[8:20].view(np.float32).reshape(4, 3)
+            assert np.array_equal(xyz, np.asarray(s.points, np.float32)[pperm[V]])
+            assert r[22] == 0 and r[23] == 0
