@@ -51,7 +51,9 @@ typedef enum {
     TM_ERR_CFACE_DUPLICATE = 6,  /* two triangles on the same tet face */
     TM_ERR_OOM = 7,              /* host or device allocation failed */
     TM_ERR_CUDA = 8,             /* a CUDA call failed; see tm_last_error() */
-    TM_ERR_TOO_LARGE = 9,        /* more than 2^31-1 tets or points, or 2^30 triangles */
+    TM_ERR_TOO_LARGE = 9,        /* a count past an index range: more than 2^31-1 tets, points
+                                    or rays, 2^30 triangles, 2^29 tets with 16-byte face
+                                    entries, or the scratch-free generator's 2^24 hits */
     TM_ERR_NO_DEVICE = 10        /* the mesh was built without upload */
 } tm_status;
 
@@ -277,7 +279,8 @@ tm_status tm_locate(const tm_mesh *mesh, const float *q, int64_t n, const int32_
  * NULL it points to a DEVICE int64 holding the ray count (read by the
  * kernel, clamped to n), so that counts produced on the device need no host
  * round trip.  opts may be NULL (defaults).  rays and hits must be 16-byte
- * aligned.  Errors: TM_ERR_ARG, TM_ERR_NO_DEVICE, TM_ERR_CUDA. */
+ * aligned.  Errors: TM_ERR_ARG, TM_ERR_NO_DEVICE, TM_ERR_CUDA, and
+ * TM_ERR_TOO_LARGE for n > 2^31 - 1 (refused before any buffer is read). */
 tm_status tm_trace(const tm_mesh *mesh, const tm_ray *rays, int64_t n, const int64_t *n_dev,
                    tm_hit *hits, const tm_trace_opts *opts, void *stream);
 

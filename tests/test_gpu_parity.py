@@ -415,6 +415,15 @@ def test_edge_cases(tmx, tiny):
     m.trace(rays, hits=hits, n_dev=torch.tensor([100], dtype=torch.int64, device="cuda"))
     h = hits.cpu().numpy()
     assert (h[100:] == -7).all() and (h[:100, 6] != -7).all()
+    # counts past the index range are refused (TM_ERR_TOO_LARGE) before any
+    # buffer is read: the walk's 2^31 rays, the scratch-free generator's 2^24 hits
+    lib = tmx.N.lib
+    assert lib.tm_trace(m._h, rays.data_ptr(), 2 ** 31, None, hits.data_ptr(), None, None) == 9
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert lib.tm_gen_secondary_noalloc(m._h, hits.data_ptr(), (1 << 24) + 1, None, 1, np.inf, 0,
+                                        rays.data_ptr(), cnt.data_ptr(), None, None) == 9
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == 0
     # hits on faces this mesh does not have (a foreign or corrupted hit buffer)
     # generate no rays: the generators treat them as misses
     g = m.trace(rays)
