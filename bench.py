@@ -16,11 +16,19 @@ same step on the same inputs.
 Other measurements on the same step (each prints its own JSON line):
   --workload medium|large|tiny|batched   other scene sizes (large: 8 AO rays per hit)
   --order hilbert|input|hilbert_regions  memory order of the mesh (Sec. 5)
-  --format tet16|tet20|tet20_aos|tet32   tet record the walk reads (Sec. 3)
+  --format tet16|tet20|tet20_aos|tet32|face|face16
+                                         record the walk reads: the paper's (Sec. 3)
+                                         or face entries (default: 16-byte ones)
   --secondary bounce|ao|shadow|reflect|refract
                                          the rays generated from the primary hits
                                          (Sec. 6; shadow rays go to a point light
                                          located on the device every step)
+
+The line also carries the walk's roofline (algorithmic bytes over its event
+time against the measured HBM copy rate, beside the L2 read rate the library's
+probe measures here), `e2e` (host rays in, host hits out, copies inside the
+timed region, two slices through a copy-in / trace / copy-out pipeline), the
+CPU oracle's rate on a bounded sample, and the SM clocks seen while timing.
 
 Prints one JSON line (rank 0).
 """
