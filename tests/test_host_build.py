@@ -285,3 +285,20 @@ def test_restart_records(tmx):
             xyz = r[8:20].view(np.float32).reshape(4, 3)
             assert np.array_equal(xyz, np.asarray(s.points, np.float32)[pperm[V]])
             assert r[22] == 0 and r[23] == 0
+
+
+def test_restart_record_of_a_boundary_triangle(tmx):
+    """A constrained triangle on the mesh boundary has a tet on one side only:
+    that side's record names it, the other side's holds T = skip = -1."""
+    pts, tets = sg.freudenthal_grid(3, 0.1, 7)
+    nbr, _, _ = oracle.OracleMesh(pts, tets, np.zeros((0, 3), np.int32)).arrays()
+    t, k = [int(x) for x in np.argwhere(nbr == -1)[0]]
+    tri = np.array([[v for j, v in enumerate(tets[t]) if j != k]], np.int32)
+    m = tmx.Mesh(pts, tets, tri, upload=False)
+    e = m.export()
+    R = m.export_restart()
+    T = R[0, :, 20]
+    assert sorted(T.tolist())[0] == -1 and (T >= 0).sum() == 1
+    side = int(np.argmax(T >= 0))
+    assert e["tet_perm"][T[side]] == t
+    assert R[0, 1 - side, 21] == -1 and R[0, side, 21] >= 0
