@@ -470,6 +470,28 @@ def test_grazing_hits_queue_for_the_final_fp64_test(tmx):
     assert ((gh["flags"][hit] & tmx.HIT_FINAL_FP64) != 0).mean() > 0.3
 
 
+def test_restart_into_a_side_without_a_tet(tmx):
+    """A constrained triangle on the mesh boundary: a ray restarted into its
+    outer side (no tet there) is flagged as a bad start and misses; one
+    restarted into the inner side walks."""
+    pts, tets = sg.freudenthal_grid(3, 0.1, 7)
+    om = oracle.OracleMesh(pts, tets, np.zeros((0, 3), np.int32))
+    nbr, _, _ = om.arrays()
+    t, k = [int(x) for x in np.argwhere(nbr == -1)[0]]
+    tri = np.array([[v for j, v in enumerate(tets[t]) if j != k]], np.int32)
+    m = tmx.Mesh(pts, tets, tri)
+    inner = int(np.argmax(m.export_restart()[0, :, 20] >= 0))
+    P = np.asarray(pts, np.float64)[tri[0]]
+    o = np.repeat(P.mean(0, keepdims=True), 2, 0).astype(np.float32)
+    centre = np.asarray(pts, np.float64)[tets[t]].mean(0)
+    inward = centre - P.mean(0)
+    d = np.stack([inward, -inward]) / np.linalg.norm(inward)
+    start = tmx.restart_start([0, 0], [inner, 1 - inner])
+    g = tmx.unpack_hits(m.trace(dev(tmx.pack_rays(o, d.astype(np.float32), np.inf, start))))
+    assert not (g["flags"][0] & tmx.HIT_BAD_START)
+    assert (g["flags"][1] & tmx.HIT_BAD_START) and g["tri"][1] == -1
+
+
 def test_axis_aligned_rays_on_unjittered_grid(tmx):
     """Rays through grid vertices and edges: exact zeros are broken by ids, walks end."""
     n = 6
