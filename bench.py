@@ -52,6 +52,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "Mrays/s (primary + diffuse-bounce) at 1 GB300 vs all-FP64 GPU path; %BW roofline"
 UNIT = "Mrays/s"
+METRIC_BATCHED = "Mrays/s, 32-mesh uneven batch in one persistent graph launch"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 RAY_BYTES, HIT_BYTES = 32, 32
@@ -622,8 +623,68 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
             **({"bruteforce": brute} if brute else {})}
 
 
+def batched_host_rays(dsc):
+    """Host rays of one batched mesh, as its device rays are made: a camera
+    grid of about half the rays, then uniform directions from interior points."""
+    import scenegen as sg
+    n_prim = dsc["primary"]
+    side = max(1, int(math.ceil(math.sqrt(n_prim))))
+    cam = sg.Camera(sg.BATCHED["camera_eye"], sg.BATCHED["fov_deg"], side,
+                    max(1, int(math.ceil(n_prim / side))))
+    o1, d1 = sg.camera_rays(cam)
+    n_uni = dsc["rays"] - n_prim
+    o = np.concatenate([o1, sg.interior_points(n_uni, dsc["seed"])]).astype(np.float32)
+    d = np.concatenate([d1, sg.uniform_directions(n_uni, dsc["seed"])]).astype(np.float32)
+    return o, d
+
+
+def run_reference_batched(args):
+    """The oracle on the batched workload: every 1024th ray of every mesh per
+    step, by brute force over the mesh's triangles (the oracle's route that
+    needs no start tet; locating millions of origins on the host would
+    dominate)."""
+    import oracle
+    import scenegen as sg
+    nthreads = oracle.default_threads()
+    stride = 1024
+    work = []
+    for dsc in sg.batched_meshes():
+        s = sg.make_grid_scene("batched", dsc["n"], sg.BATCHED["jitter"], dsc["seed"],
+                               n_spheres=dsc["n_spheres"])
+        o, d = batched_host_rays(dsc)
+        work.append((oracle.OracleTriangles(s.points, s.tris), o[::stride], d[::stride]))
+
+    def step():
+        for ts, o, d in work:
+            ts.bruteforce(o, d, np.inf, nthreads=nthreads)
+        return sum(len(o) for _, o, _ in work)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.time()
+    traced = sum(step() for _ in range(args.steps))
+    dt = time.time() - t0
+    value = traced / dt / 1e6
+    sample = (f"every {stride}th ray of each of the 32 meshes ({traced // args.steps} rays a step), "
+              "brute force over the mesh's triangles")
+    print(json.dumps({"impl": "reference", "metric": METRIC_BATCHED,
+                      "value": round(value, 4), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+                      "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"batched: {WORKLOADS['batched']['desc']}",
+                                 "mode": "FP64 oracle, brute force"},
+                      "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": nthreads,
+                                       "kind": "oracle", "sample": sample},
+                      "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
+        return
+    if args.workload == "batched":
+        run_reference_batched(args)
         return
     import oracle
     W = WORKLOADS[args.workload]
@@ -741,7 +802,7 @@ def run_batched(args, world, rank, local):
         return
     total = total_all
     value = total / (ms_graph * 1e-3) / 1e6
-    line = {"metric": "Mrays/s, 32-mesh uneven batch in one persistent graph launch", "value": round(value, 2),
+    line = {"metric": METRIC_BATCHED, "value": round(value, 2),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 3,
             "ms_per_step": round(ms_graph, 3), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -61,3 +61,14 @@ def test_cpu_baseline_sizes_its_sample_and_times_brute_force():
     assert "every 1th pixel" in cb["sample"]          # the whole 64x64 frame fits the budget
     assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
     assert cb["bruteforce"]["value"] > 0 and "192 triangles" in cb["bruteforce"]["sample"]
+
+
+def test_reference_arm_on_the_batched_workload():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "batched",
+                          "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True,
+                         text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC_BATCHED
+    assert line["value"] > 0 and line["scaling"] == "strong"
+    assert "brute force" in line["cpu_baseline"]["sample"]
