@@ -623,6 +623,11 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
             **({"bruteforce": brute} if brute else {})}
 
 
+def sig4(x):
+    """x to four significant digits (the oracle's rates span 1e-4 to 10 Mrays/s)."""
+    return float(f"{x:.4g}")
+
+
 def batched_host_rays(dsc):
     """Host rays of one batched mesh, as its device rays are made: a camera
     grid of about half the rays, then uniform directions from interior points."""
@@ -668,15 +673,15 @@ def run_reference_batched(args):
     sample = (f"every {stride}th ray of each of the 32 meshes ({traced // args.steps} rays a step), "
               "brute force over the mesh's triangles")
     print(json.dumps({"impl": "reference", "metric": METRIC_BATCHED,
-                      "value": round(value, 4), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "value": sig4(value), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
                       "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                       "dtype": "f64", "data": "synthetic",
                       "config": {"workload": f"batched: {WORKLOADS['batched']['desc']}",
                                  "mode": "FP64 oracle, brute force"},
-                      "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": nthreads,
+                      "cpu_baseline": {"value": sig4(value), "unit": UNIT, "cores": nthreads,
                                        "kind": "oracle", "sample": sample},
-                      "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                      "e2e": {"value": sig4(value), "unit": UNIT, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
@@ -689,31 +694,41 @@ def run_reference(args, world, rank):
     import oracle
     W = WORKLOADS[args.workload]
     s = build_scene(args.workload)
-    om = oracle.OracleMesh(s.points, s.tets, s.tris)
-    om.ctet_cache = om.arrays()[2]
     nthreads = oracle.default_threads()
-    cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
     n = s.camera.width * s.camera.height
-    stride = 16                                   # a bounded sample: every 16th pixel per step
+    # a mesh whose tet adjacency is too large to build on the host (the large
+    # scene) takes the oracle's brute force over all triangles instead
+    brute = s.n_tets > 20_000_000
+    if brute:
+        om = oracle.OracleTriangles(s.points, s.tris)
+        cam_tet = [-1]
+        stride = 16384                            # a bounded sample: every 16384th pixel per step
+    else:
+        om = oracle.OracleMesh(s.points, s.tets, s.tris)
+        om.ctet_cache = om.arrays()[2]
+        cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
+        stride = 16                               # a bounded sample: every 16th pixel per step
     sel = np.arange(0, n, stride)
     for _ in range(args.warmup):
-        oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+        oracle_step(om, s, W, cam_tet[0], sel, nthreads, brute=brute)
     t0 = time.time()
     traced = 0
     for _ in range(args.steps):
-        traced += oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+        traced += oracle_step(om, s, W, cam_tet[0], sel, nthreads, brute=brute)
     dt = time.time() - t0
     value = traced / dt / 1e6
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+    line = {"impl": "reference", "metric": METRIC, "value": sig4(value), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {W['desc']}", "mode": "FP64 oracle walk"},
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": nthreads,
+            "config": {"workload": f"{args.workload}: {W['desc']}",
+                       "mode": "FP64 oracle, brute force" if brute else "FP64 oracle walk"},
+            "cpu_baseline": {"value": sig4(value), "unit": UNIT, "cores": nthreads,
                              "kind": "oracle",
                              "sample": f"every {stride}th pixel ({len(sel)} primary rays) + their "
-                                       f"{W['kind']} rays per step"},
-            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       f"{W['kind']} rays per step"
+                                       + (", brute force over all triangles" if brute else "")},
+            "e2e": {"value": sig4(value), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
