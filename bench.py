@@ -561,43 +561,50 @@ def oracle_step(om, s, W, cam_tet, sel, nthreads, brute=False):
 def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
     import oracle
     nthreads = oracle.default_threads()
-    if om is None:
-        om = oracle.OracleMesh(s.points, s.tets, s.tris)
-    om.ctet_cache = om.arrays()[2]
-    cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
+    # a mesh whose tet adjacency is too large to build on the host (the large
+    # scene) takes the oracle's brute force over all triangles instead
+    big = s.n_tets > 20_000_000
+    if big:
+        om = oracle.OracleTriangles(s.points, s.tris)
+        cam_tet = [-1]
+    else:
+        if om is None:
+            om = oracle.OracleMesh(s.points, s.tets, s.tris)
+        om.ctet_cache = om.arrays()[2]
+        cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
     n = s.camera.width * s.camera.height
     stride = 1
     # size the sample: first a small probe, then as many pixels as fit the budget
-    probe = np.arange(0, n, max(1, n // 20000))
+    probe = np.arange(0, n, max(1, n // (16 if big else 20000)))
     t0 = time.time()
-    oracle_step(om, s, W, cam_tet[0], probe, nthreads)
+    oracle_step(om, s, W, cam_tet[0], probe, nthreads, brute=big)
     rate = len(probe) / max(time.time() - t0, 1e-6)
     want = int(rate * budget_s)
     if want < n:
         stride = max(1, int(math.ceil(n / max(want, 1))))
     sel = np.arange(0, n, stride)
     t0 = time.time()
-    traced = oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+    traced = oracle_step(om, s, W, cam_tet[0], sel, nthreads, brute=big)
     dt = time.time() - t0
     if dt < budget_s / 2 and stride > 1:
         # the small probe underestimates the rate: size the sample again from this run
         stride = max(1, int(math.ceil(n / max(1, int(len(sel) / dt * budget_s)))))
         sel = np.arange(0, n, stride)
         t0 = time.time()
-        traced = oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+        traced = oracle_step(om, s, W, cam_tet[0], sel, nthreads, brute=big)
         dt = time.time() - t0
     passes = 1
     while stride == 1 and dt < budget_s / 2 and passes < 16:
         # the whole frame takes less than the budget: trace it again
         t0 = time.time()
-        traced += oracle_step(om, s, W, cam_tet[0], sel, nthreads)
+        traced += oracle_step(om, s, W, cam_tet[0], sel, nthreads, brute=big)
         dt += time.time() - t0
         passes += 1
     # the same walk on one core, on a sample 4 x cores times sparser
     stride1 = max(1, stride * nthreads * 4)
     one = np.arange(0, n, stride1)
     t1 = time.time()
-    traced1 = oracle_step(om, s, W, cam_tet[0], one, 1)
+    traced1 = oracle_step(om, s, W, cam_tet[0], one, 1, brute=big)
     dt1 = time.time() - t1
     brute = None
     if workload == "tiny":
@@ -610,13 +617,14 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
                  "sample": f"the whole {s.camera.width}x{s.camera.height} image + its {W['kind']} "
                            f"rays, Moller-Trumbore against all {s.n_tris} triangles; {tb} rays "
                            f"in {db:.2f} s"}
-    return {"value": round(traced / dt / 1e6, 4), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+    return {"value": sig4(traced / dt / 1e6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"every {stride}th pixel of the {s.camera.width}x{s.camera.height} image "
                       f"({len(sel)} primary rays) + their {W['kind']} rays"
                       + (f", {passes} passes" if passes > 1 else "")
-                      + f"; {traced} rays in {dt:.1f} s (FP64 face-plane walk, numpy "
-                        "secondary-ray generation)",
-            "single_core": {"value": round(traced1 / dt1 / 1e6, 4), "unit": UNIT, "cores": 1,
+                      + f"; {traced} rays in {dt:.1f} s ("
+                      + ("FP64 brute force over all triangles" if big else "FP64 face-plane walk")
+                      + ", numpy secondary-ray generation)",
+            "single_core": {"value": sig4(traced1 / dt1 / 1e6), "unit": UNIT, "cores": 1,
                             "sample": f"every {stride1}th pixel "
                                       f"({len(one)} primary rays) + their {W['kind']} rays; "
                                       f"{traced1} rays in {dt1:.1f} s"},
