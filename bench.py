@@ -537,7 +537,9 @@ def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world, f
 
 def oracle_step(om, s, W, cam_tet, sel, nthreads, brute=False):
     """One step of the workload on the host oracle for the pixels `sel`; returns rays traced.
-    brute: nearest triangle over all of them instead of the walk (tiny scenes only)."""
+    brute: nearest triangle over all of them instead of the walk: the brute-force
+    comparison on the tiny scene, and the route for the large scene, whose tet
+    adjacency is too large to build on the host."""
     import scenegen as sg
     from oracle.secondary import arrival_side, hit_side, secondary_rays
     o, d = sg.camera_rays(s.camera)
@@ -680,6 +682,9 @@ def run_reference_batched(args):
     value = traced / dt / 1e6
     sample = (f"every {stride}th ray of each of the 32 meshes ({traced // args.steps} rays a step), "
               "brute force over the mesh's triangles")
+    # "strong", as the GPU arm of this workload reports: its 32 meshes are one
+    # fixed job that more ranks split between them, while the single-frame
+    # workloads give every replica a whole frame of its own ("weak")
     print(json.dumps({"impl": "reference", "metric": METRIC_BATCHED,
                       "value": sig4(value), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),

@@ -5,12 +5,12 @@
  * (arXiv 2103.02309).
  *
  * The library builds the compact mesh records of Sec. 3 (16-byte Tet16
- * records, Fig. "Tet16 structure", plus 16-byte aligned float4 points),
+ * records, the layout of the Tet16 figure, plus 16-byte aligned float4 points),
  * orders points and tets along a Hilbert curve (Sec. 5), locates points
  * with the walk of Sec. 4.2, and traces rays with the 2-D exit-face walk of
  * Sec. 4 (Alg. 1, Alg. 6-7, the scaled basis of Eq. 1-3 and the projected
  * origin of Sec. 7, optimisation 1), stopping at the first constrained face
- * (Sec. 3, last paragraph; Sec. 4, "terminate the traversal").  Secondary
+ * it crosses (Sec. 3, last paragraph; Sec. 4).  Secondary
  * rays restart from a hit face into an adjacent tet (Sec. 6).
  *
  * Plain C types only: every pointer is either a host pointer or a CUDA
@@ -374,8 +374,12 @@ tm_status tm_gen_specular(const tm_mesh *mesh, const tm_ray *rays_in, const tm_h
  * TM_NOALLOC_MAX_HITS hits (about 192 KiB, held on every device that loads
  * the library until the process exits).  n > TM_NOALLOC_MAX_HITS returns
  * TM_ERR_TOO_LARGE (tm_last_error() says why) and launches nothing.
- * The first call on each device looks up the array's device address; make
- * that first call outside any stream capture.  All calls share the array,
+ * The first call on each device looks up the array's device address and
+ * keeps it for the life of the process; make that first call outside any
+ * stream capture.  cudaDeviceReset (or any other teardown of the device's
+ * primary context) unloads the library's module from that device and
+ * leaves the kept address stale: do not call this function on a device
+ * after resetting it in the same process.  All calls share the array,
  * so calls whose work overlaps on the GPU (several streams or host
  * threads) race on it: serialise them.  Nothing in the array needs to start
  * at zero; each call writes every entry it later reads. */

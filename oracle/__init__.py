@@ -58,6 +58,8 @@ def _bind(lib):
     lib.orc_bruteforce.argtypes = [P, i64, P, P, P, P, ctypes.c_int] + [P] * 4
     lib.orc_locate.argtypes = [P, i64, P, ctypes.c_int, P, P]
     lib.orc_tet_bary.argtypes = [P, ctypes.c_int32, P, P]
+    lib.orc_mesh_relink.argtypes = [P, i64, ctypes.c_int, ctypes.c_int32, ctypes.c_int]
+    lib.orc_mesh_relink.restype = ctypes.c_int
     return lib
 
 
@@ -135,6 +137,11 @@ class OracleMesh:
     def count_boundary(self):
         return int(self.lib.orc_count_boundary(self._h))
 
+    def relink(self, t, k, u, ku):
+        """Test hook: overwrite the link of tet t across face k with (u, ku)."""
+        if self.lib.orc_mesh_relink(self._h, int(t), int(k), int(u), int(ku)) != 0:
+            raise OracleError("relink: bad arguments")
+
     def trace(self, o, d, tmax, start, entry=None, max_steps=None, nthreads=None):
         """Definitional FP64 walk.  entry = 2*c + side restarts through triangle c (else -1)."""
         o = np.ascontiguousarray(o, dtype=np.float32).reshape(-1, 3)
@@ -203,5 +210,5 @@ class OracleTriangles(OracleMesh):
     def _tetless(self, *a, **k):
         raise OracleError("a triangle set has no tets")
 
-    trace = locate = arrays = tet_bary = _tetless
+    trace = locate = arrays = tet_bary = relink = _tetless
     count_nonpositive = count_asymmetric = count_boundary = _tetless

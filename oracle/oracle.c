@@ -268,6 +268,19 @@ int64_t orc_count_asymmetric(const orc_mesh *m) {
     return bad;
 }
 
+/* Test hook for the checkers' pins: overwrites the link of tet t across its
+ * face k with (u, ku), the neighbour and the index of the shared face inside
+ * it (u = -1 for the boundary), so that a test can plant a broken adjacency
+ * and see orc_count_asymmetric report it.  Returns 1 on bad arguments. */
+int orc_mesh_relink(orc_mesh *m, int64_t t, int k, int32_t u, int ku) {
+    if (!m || !m->nbr || t < 0 || t >= m->nt || k < 0 || k > 3 || u < -1 || u >= m->nt ||
+        ku < -1 || ku > 3)
+        return 1;
+    m->nbr[4 * t + k] = u;
+    m->nbrk[4 * t + k] = u < 0 ? -1 : ku;
+    return 0;
+}
+
 /* Number of boundary faces (no neighbour). */
 int64_t orc_count_boundary(const orc_mesh *m) {
     int64_t nb = 0;

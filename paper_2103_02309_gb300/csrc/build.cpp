@@ -15,7 +15,7 @@
 //     non-constrained face graph that holds them (a concurrent union-find);
 //  5. packing: cold records (V0..V3, N0..N3) and Tet16 records
 //     (VX = V0^V1^V2^V3; NX_j = N_j ^ N_3 with the neighbours sorted by the
-//     id of the vertex they sit across, Sec. 3 "Tet20"/"Tet16").
+//     id of the vertex they sit across, Sec. 3, the Tet20 and Tet16 layouts).
 #include <omp.h>
 #include <parallel/algorithm>
 

@@ -10,9 +10,9 @@
 #include "../../include/tetmesh.h"
 
 // A neighbour field holds a tet id (bit 31 clear) or a flagged constrained
-// face (Sec. 3: "a single bitmask ... the remaining 31 bits reference either a
-// neighbouring tetrahedron or a constrained face").  The mesh boundary is the
-// flagged reserved id 0x7FFFFFFF.
+// face (Sec. 3: the top bit tells the two apart and the low 31 bits index a
+// tet or a constrained face).  The mesh boundary is the flagged reserved id
+// 0x7FFFFFFF.
 #define TM_CFACE_FLAG 0x80000000u
 #define TM_BOUNDARY 0xFFFFFFFFu
 

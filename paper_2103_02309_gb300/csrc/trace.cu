@@ -51,11 +51,19 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBatch = 64;
 
 // The hit slot between the phases, 8 words:
-//   [0] phase (0: walk from here, 1: ended, 2: parked at tet [1] for a re-decided step)
+//   [0] phase: 1 ended, 2 parked at tet [1] for a re-decided step; a walk
+//       record (walk from here) holds -1 - (the tet the ray comes from),
+//       which is negative, so that a bounded walk that ends before its first
+//       step can name the tet its segment ends in whatever record it reads
 //   [1] tet (walk: tet to enter; ended: last tet)
 //   [2] walk: prev (Tet16 and the paper's other records) or the fourth vertex
 //       of tet [1] (face entries); ended: the flagged value that ended the walk
 //   [3..5] entry face ids, counter-clockwise in the ray's basis  [6] steps  [7] flags
+constexpr int kPhaseEnded = 1, kPhaseParked = 2;
+__device__ __forceinline__ int walk_phase(int32_t from) { return -1 - from; }
+__device__ __forceinline__ bool is_walk_phase(int w) { return w < 0; }
+__device__ __forceinline__ int32_t walk_from(int w) { return -1 - w; }
+
 __device__ __forceinline__ void put_record(tm_hit *hp, int phase, int32_t tet, uint32_t prev_or_code,
                                            int32_t i0, int32_t i1, int32_t i2, uint32_t steps,
                                            uint32_t flags) {
@@ -65,7 +73,7 @@ __device__ __forceinline__ void put_record(tm_hit *hp, int phase, int32_t tet, u
 
 __device__ __forceinline__ void put_end(tm_hit *hp, int32_t tet, uint32_t code, uint32_t steps,
                                         uint32_t flags) {
-    put_record(hp, 1, tet, code, -1, -1, -1, steps, flags);
+    put_record(hp, kPhaseEnded, tet, code, -1, -1, -1, steps, flags);
 }
 
 // Which mesh and which ray a global ray index names (batched launches).
@@ -221,9 +229,10 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
         // the face-entry walk starts from the next tet's fourth vertex
         const int4 cv = __ldg(mv.cold + 2 * (int64_t)next);
         const int32_t i3 = cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2;
-        put_record(hp, 0, (int32_t)next, (uint32_t)i3, S.i0, S.i1, S.i2, steps, sc.flags);
+        put_record(hp, walk_phase(T), (int32_t)next, (uint32_t)i3, S.i0, S.i1, S.i2, steps, sc.flags);
     } else
-        put_record(hp, 0, (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
+        put_record(hp, walk_phase(T), (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps,
+                   sc.flags);
 }
 
 // The start phase chases three or four dependent reads per ray (the ray,
@@ -278,7 +287,7 @@ __device__ __forceinline__ bool finish_one(const MeshView &mv, const tm_ray *rp,
     uint32_t code = (uint32_t)e0.z;
     const uint32_t steps = (uint32_t)e1.z;
     uint32_t flags = (uint32_t)e1.w;
-    if (e0.x != 1) {  // the walk never ended this ray (cannot happen for a completed launch)
+    if (e0.x != kPhaseEnded) {  // the walk never ended this ray (cannot happen for a completed launch)
         code = TM_BOUNDARY;
         flags |= TM_HIT_BAD_ID;
     }
@@ -606,7 +615,7 @@ __device__ __noinline__ void resolve_parked(const MeshView mv, const tm_ray *rp,
             const int4 cv = __ldg(mv.cold + 2 * (int64_t)next);
             w2 = (uint32_t)(cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2);
         }
-        put_record(hp, 0, (int32_t)next, w2, S.i0, S.i1, S.i2, steps, sc.flags);
+        put_record(hp, walk_phase(S.tet), (int32_t)next, w2, S.i0, S.i1, S.i2, steps, sc.flags);
     }
 }
 
@@ -780,7 +789,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
             const int4 b = __ldcg(reinterpret_cast<const int4 *>(hp) + 1);
             const float4 w0 = __ldg(reinterpret_cast<const float4 *>(sc.ray));
             const float4 w1 = __ldg(reinterpret_cast<const float4 *>(sc.ray) + 1);
-            if (a.x == 0) {
+            if (is_walk_phase(a.x)) {
                 S.tet = a.y;
                 S.prev = a.z;
                 S.i0 = a.w;
@@ -804,8 +813,8 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     Z.set(0, x0);
                     Z.set(1, x1);
                     Z.set(2, x2);
-                    if (Z.beyond()) {
-                        put_end(hp, S.prev, TM_BOUNDARY, steps, sc.flags);
+                    if (Z.beyond()) {  // the segment ends in the tet the ray comes from
+                        put_end(hp, walk_from(a.x), TM_BOUNDARY, steps, sc.flags);
                         active = false;
                     }
                 }
@@ -956,7 +965,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 // since entering the tet, then one 32-byte read ----
                 const uint32_t sig = step_signs<MODE, MODE == FP32G && !GuardInLoop<FMT>::value, false>(S, S.p3, S.i3, S.m3, sc);
                 if (MODE == FP32G && !GuardInLoop<FMT>::value && sig == kParked) {
-                    put_record(hp, 2, S.tet, (uint32_t)S.i3, S.i0, S.i1, S.i2, steps, sc.flags);
+                    put_record(hp, kPhaseParked, S.tet, (uint32_t)S.i3, S.i0, S.i1, S.i2, steps, sc.flags);
                     active = false;
                     parked = true;
                     continue;
@@ -1025,7 +1034,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 if (MODE == FP32G && sig == kParked) {
                     // undecided in float32: park the ray; the lane re-decides this
                     // step out of line at its next refill
-                    put_record(hp, 2, S.tet, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
+                    put_record(hp, kPhaseParked, S.tet, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps, sc.flags);
                     active = false;
                     parked = true;
                     continue;

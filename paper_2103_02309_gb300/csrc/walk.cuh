@@ -22,8 +22,8 @@
 //    that of the triple product (A x B).d: no basis, no division.
 //  * Exit face (Alg. 1): with the entry face p0, p1, p2 counter-clockwise
 //    around the origin, the new vertex p3 replaces slot e, and the kept
-//    face is again counter-clockwise (Sec. 4: "the counterclockwise
-//    ordering is always preserved").
+//    face is again counter-clockwise (Sec. 4: replacing a slot keeps the
+//    winding, so no reordering is ever needed).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -197,8 +197,8 @@ template <class R> struct WalkState {
 
 
 
-// Exit face of tet T for the ray's line (Sec. 4: "at most four point in
-// triangle tests in 2-D"): the face, other than `skip`, whose projection
+// Exit face of tet T for the ray's line (Sec. 4: the first tet needs up to
+// four 2-D triangle tests): the face, other than `skip`, whose projection
 // holds the origin with clockwise order in its inward orientation.  On
 // success fills the state (entry face of the next tet, counter-clockwise)
 // and returns the raw neighbour value across it; returns false when no

@@ -42,8 +42,11 @@ def hit_points(points, tris, tri, b1, b2):
     return (1.0 - b1 - b2) * v0 + b1 * v1 + b2 * v2
 
 
-def compare(points, tris, gpu: dict, orc: dict, t_rtol=T_RTOL, check_t=True):
-    """Returns a stats dict; raises AssertionError when the bar is not met."""
+def compare(points, tris, gpu: dict, orc: dict, t_rtol=T_RTOL, check_t=True, rate_bar=True):
+    """Returns a stats dict; raises AssertionError when the bar is not met.
+    rate_bar=False keeps every other check but not the 99.999 % agreement
+    rate, for inputs built to put hits exactly on triangle edges, where
+    every mismatch is an excused tie."""
     g_tri, o_tri = np.asarray(gpu["tri"]), np.asarray(orc["tri"])
     n = len(g_tri)
     same = g_tri == o_tri
@@ -82,7 +85,8 @@ def compare(points, tris, gpu: dict, orc: dict, t_rtol=T_RTOL, check_t=True):
     # every mismatch excused, and at least 99.999 % identical (at least one
     # excused mismatch allowed for small batches)
     assert unexcused == 0, stats
-    assert len(bad) <= max(1, int(np.ceil((1 - ID_AGREEMENT) * n))), stats
+    if rate_bar:
+        assert len(bad) <= max(1, int(np.ceil((1 - ID_AGREEMENT) * n))), stats
     if check_t:
         assert stats["max_rel_t"] <= t_rtol, stats
         assert stats["max_point_err"] <= POINT_TOL, stats

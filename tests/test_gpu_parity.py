@@ -239,7 +239,7 @@ def test_record_formats_identical(tmx, mode):
         keep = mb > 1e-7
         d = g.normal(size=(3000, 3))
         d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
-        for tmax in (np.inf, 0.2):
+        for tmax in (np.inf, 0.2, 0.03):
             rays = dev(tmx.pack_rays(q[keep], d[keep], tmax, tinv[start[keep]]))
             got = {f: tmx.unpack_hits(mesh.trace(rays, mode=mode, format=f,
                                                  tmax_early_exit=np.isfinite(tmax)))
@@ -249,6 +249,39 @@ def test_record_formats_identical(tmx, mode):
                     assert np.array_equal(got[f][k], got["tet16"][k]), (f, k)
             w = om.trace(q[keep], d[keep], tmax, start[keep])
             compare(scene.points, scene.tris, got["tet32"], w, check_t=(mode != "fp32"))
+
+
+@pytest.mark.parametrize("mode", ["fp32g", "fp64"])
+def test_bounded_misses_end_in_the_tet_of_the_segment_end(tmx, tiny, mode):
+    """Ambient-occlusion rays (t_max 0.05, shorter than a cell) restarted from
+    the oracle's primary hits, walked with the early exit at t_max: many end
+    before their first step.  Every record format reports the same tet for
+    every ray.  A miss that ended before its first step ends in its start
+    tet, the tet on the restart side of the hit triangle (the oracle's
+    adjacency), which holds the segment's end o + t_max d (the oracle's
+    barycentrics)."""
+    s = tiny.s
+    mesh = tmx.Mesh(s.points, s.tets, s.tris, tet20=True, faces=True, faces16=True)
+    tperm = mesh.export()["tet_perm"]
+    o, d = sg.camera_rays(s.camera)
+    w = tiny.oracle_trace(o, d, np.inf, tiny.cam_in[0])
+    o2, d2, tm2, entry, _ = oracle_secondary(tiny, w, 8, 0.05, seed=21)
+    rays = dev(tmx.pack_rays(o2, d2, tm2, -1 - entry))
+    got = {f: tmx.unpack_hits(mesh.trace(rays, mode=mode, format=f, tmax_early_exit=True))
+           for f in ("tet16", "tet20", "tet20_aos", "tet32", "face", "face16")}
+    for f in got:
+        for k in ("tri", "t", "tet", "steps", "flags"):
+            assert np.array_equal(got[f][k], got["tet16"][k]), (f, k)
+    g = got["face16"]
+    compare(s.points, s.tris, g, tiny.oracle_trace(o2, d2, tm2, -1, entry))
+    assert (g["tet"] >= 0).all() and (g["tet"] < s.n_tets).all()
+    first = (g["tri"] < 0) & (g["steps"] == 0)
+    assert first.sum() > 100
+    side_tet = tiny.ctet[entry[first] >> 1, entry[first] & 1]
+    assert np.array_equal(tperm[g["tet"][first]], side_tet)
+    end = o2[first].astype(np.float64) + tm2[first, None].astype(np.float64) * d2[first]
+    worst = min(tiny.om.tet_bary(int(t), x).min() for t, x in zip(side_tet, end))
+    assert worst > -1e-5
 
 
 @pytest.mark.parametrize("other", ["input", "hilbert_regions"])
@@ -266,6 +299,12 @@ def test_hilbert_and_other_orders_identical(tmx, other):
     for k in ("tri", "t", "b1", "b2", "steps"):
         assert np.array_equal(ga[k][~tie], gb[k][~tie]), k
     assert np.array_equal(a.tperm[ga["tet"]][~tie], b.tperm[gb["tet"]][~tie])
+    # both orders against the oracle walk, every ray
+    w = a.oracle_trace(o, d, np.inf, cin[0])
+    compare(s.points, s.tris, ga, w)
+    compare(s.points, s.tris, gb, w)
+    hit = w["tri"] >= 0
+    assert np.array_equal(b.tperm[gb["tet"]][hit], w["tet"][hit])
 
 
 def test_medium_full_size_orders_and_oracle(tmx):
@@ -493,7 +532,10 @@ def test_restart_into_a_side_without_a_tet(tmx):
 
 
 def test_axis_aligned_rays_on_unjittered_grid(tmx):
-    """Rays through grid vertices and edges: exact zeros are broken by ids, walks end."""
+    """Rays through grid vertices and edges: exact zeros are broken by ids,
+    walks end, and every ray, misses included, equals the oracle's walk up to
+    ties on a triangle edge (a mismatch is excused only when the hit lies
+    within 1e-6 of an edge of its triangle)."""
     n = 6
     pts, tets = sg.freudenthal_grid(n, 0.0, 1)
     tris = sg.constrained_faces(n, sg.slab_cells(n, 4))
@@ -511,3 +553,5 @@ def test_axis_aligned_rays_on_unjittered_grid(tmx):
             # every reported hit lies on the plane z = 4h and on its triangle
             z0 = np.float32(4 / n)
             assert np.allclose(o[hit, 2] + gh["t"][hit] * d[hit, 2], z0, atol=1e-6)
+            w = c.oracle_trace(o, d, np.inf, start)
+            compare(c.s.points, c.s.tris, gh, w, check_t=(mode != "fp32"), rate_bar=False)

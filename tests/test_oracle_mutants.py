@@ -22,6 +22,7 @@ PIN_CASES = [
     (pins.test_closed_form_sphere, {}),
     (pins.test_restart_rays_equal_bruteforce, {}),
     (pins.test_locate_contains_point, {}),
+    (pins.test_asymmetry_checker_counts_planted_links, {}),
 ]
 
 MUTANTS = {
@@ -33,6 +34,12 @@ MUTANTS = {
     "tmax_ignored": ("if (tbest > tmax) break;", "(void)tmax;"),
     "side_flipped": ("m->ctet[2 * c + (s > 0 ? 0 : 1)] = t;", "m->ctet[2 * c + (s > 0 ? 1 : 0)] = t;"),
     "wrong_neighbour_face": ("kin = m->nbrk[4 * T + best];", "kin = best;"),
+    # the builder writes a wrong back-link index for one side of every face
+    "nbrk_backlink": ("m->nbrk[o1] = o0 % 4;", "m->nbrk[o1] = (o0 + 1) % 4;"),
+    # the symmetry checker loses its back-link test, or its vertex comparison
+    "asym_no_backlink_check": ("if (m->nbr[4 * u + ku] != t) { ++bad; continue; }",
+                               "if (m->nbr[4 * u + ku] != t) { continue; }"),
+    "asym_no_vertex_check": ("if (a != x || b != y || c != z) ++bad;", "(void)x; (void)y; (void)z;"),
 }
 
 
@@ -52,6 +59,19 @@ def build_variant(tmp_path, name, old, new):
     path = tmp_path / f"{name}.c"
     path.write_text(src.replace(old, new))
     return oracle.load(oracle.build(str(path), str(tmp_path / f"lib{name}.so")))
+
+
+def test_broken_backlink_is_reported_by_the_checker(tmp_path, monkeypatch):
+    """With the builder's back-link broken, the symmetry checker itself (not
+    only the walk pins) reports the broken links on a valid mesh."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc missing")
+    import scenegen as sg
+    lib = build_variant(tmp_path, "nbrk_backlink", *MUTANTS["nbrk_backlink"])
+    s = sg.make_config("tiny")
+    m = oracle.OracleMesh(s.points, s.tets, s.tris, lib=lib)
+    interior = 4 * s.n_tets - 12 * s.n * s.n
+    assert m.count_asymmetric() >= interior // 2
 
 
 def test_unmodified_oracle_passes_pins():

@@ -76,6 +76,31 @@ def test_invariants_tiny():
     assert ((fc >= 0).sum()) == 2 * s.n_tris
 
 
+def test_asymmetry_checker_counts_planted_links():
+    """The neighbour-symmetry checker is a detector, not a constant: swap the
+    links of one interior tet across two of its faces.  Its own two links
+    now name a neighbour that points back through a face with other
+    vertices (caught by the vertex comparison), and its two former
+    neighbours point to a tet that no longer points back (caught by the
+    back-link test): exactly four defects."""
+    s = sg.make_config("tiny")
+    m = oracle.OracleMesh(s.points, s.tets, s.tris)
+    assert m.count_asymmetric() == 0
+    nbr, _, _ = m.arrays()
+    t = int(np.nonzero((nbr >= 0).all(axis=1))[0][0])
+    k1, k2 = 0, 1
+    u1, u2 = int(nbr[t, k1]), int(nbr[t, k2])
+    ku1 = int(np.nonzero(nbr[u1] == t)[0][0])
+    ku2 = int(np.nonzero(nbr[u2] == t)[0][0])
+    m.relink(t, k1, u2, ku2)
+    m.relink(t, k2, u1, ku1)
+    assert m.count_asymmetric() == 4
+    # a one-sided link to the boundary: its old neighbour no longer sees a link back
+    m2 = oracle.OracleMesh(s.points, s.tets, s.tris)
+    m2.relink(t, k1, -1, -1)
+    assert m2.count_asymmetric() == 1
+
+
 def test_rejects_bad_meshes():
     pts, tets = sg.freudenthal_grid(2, 0.0, 1)
     tris = np.array([[0, 1, 2]], np.int32)                  # not a face of the Kuhn split

@@ -68,11 +68,11 @@ def test_noalloc_matches_allocating_entry_point():
     # a request beyond the static capacity is refused before any work is launched
     big = TM_NOALLOC_MAX_HITS + 1
     dummy = torch.empty((1, 8), dtype=torch.int32, device="cuda")
-    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    count = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     status = fn(mesh.handle, ctypes.c_void_p(dummy.data_ptr()), big, None, 1, float("inf"), 0,
                 ctypes.c_void_p(dummy.data_ptr()), ctypes.c_void_p(count.data_ptr()), None,
                 ctypes.c_void_p(stream.cuda_stream))
     assert status == TM_ERR_TOO_LARGE
     assert "capacity" in N.lib.tm_last_error().decode()
     torch.cuda.synchronize()
-    assert int(count.item()) == 0
+    assert int(count.item()) == -1          # untouched: nothing was launched or written
