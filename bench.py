@@ -60,9 +60,17 @@ RAY_BYTES, HIT_BYTES = 32, 32
 # tet record (RECORD_BYTES of the format the walk reads) and one float4
 # point; per ray its start record (32 B, in the hit slot), the ray (32 B),
 # the three entry-face points (48 B) and the end record (32 B).
-WALK_RAY_BYTES = 32 + RAY_BYTES + 3 * 16 + 32
+# The method's algorithmic bytes (the paper's compact layout, whatever record
+# the walk reads): per tet step the 16-byte Tet16 record and the 16-byte
+# float4 point of the new vertex; per ray its 36-byte ray, 32-byte hit, the
+# start tet's 32-byte full record and four 16-byte points, and the 24-byte
+# triangle record of the hit.
+METHOD_STEP_BYTES = 16 + 16
+METHOD_RAY_BYTES = 36 + 32 + 32 + 4 * 16 + 24
+# What the walk kernel of each record format reads per step (record + point).
 RECORD_BYTES = {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32, "face": 32, "face16": 16}
 POINT_BYTES = {"face": 0, "face16": 0}   # face entries carry the new vertex; the others read a point
+MODE_NAMES = {"fp32g": "FP32 walk + FP64 guard", "fp32": "pure FP32", "fp64": "all FP64"}
 # Rays generated from each hit: (rays per hit, tmax); None = per-ray (shadow)
 SECONDARY = {"bounce": (1, float("inf")), "ao": (8, 0.05), "shadow": (1, None),
              "reflect": (1, float("inf")), "refract": (1, float("inf"))}
@@ -118,17 +126,32 @@ def dist_env():
     return world, rank, local
 
 
+def read_probe(torch, buf, reps, sink):
+    """The benchmark's read-bandwidth probe (libtmprobe.so, built beside the
+    library and kept out of its C ABI): `reps` passes over `buf`."""
+    import ctypes
+    from paper_2103_02309_gb300 import build as libbuild
+    lib = ctypes.CDLL(libbuild.PROBE_LIB)
+    fn = lib.tm_bench_read_probe
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    st = fn(buf.data_ptr(), buf.numel() * buf.element_size(), int(reps), sink.data_ptr(),
+            torch.cuda.current_stream().cuda_stream)
+    if st != 0:
+        raise RuntimeError(f"tm_bench_read_probe failed with status {st}")
+
+
 def measured_l2(torch, tmx, dev, mib=48, reps=40):
     """Read bandwidth of a buffer resident in L2 (GB/s): the L2 roofline of
-    workloads whose records fit in L2.  The library's read probe over `mib`
-    MiB, first passes untimed so the buffer is resident, then `reps` timed."""
+    workloads whose records fit in L2.  The read probe over `mib` MiB, first
+    passes untimed so the buffer is resident, then `reps` timed."""
     x = torch.ones(mib * (1 << 20) // 4, dtype=torch.float32, device=dev)
     sink = torch.zeros(1, dtype=torch.int32, device=dev)
-    tmx.read_probe(x, 3, sink)
+    read_probe(torch, x, 3, sink)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    tmx.read_probe(x, reps, sink)
+    read_probe(torch, x, reps, sink)
     e1.record()
     e1.synchronize()
     return x.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
@@ -161,24 +184,70 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, variant=""):
-    """DRAM bytes per trace launch from the committed ncu summary, if it matches the source."""
+def profiled_counters(workload, variant=""):
+    """ncu counters per walk launch from the committed summary
+    (profiles/walk_kernel_<workload>.md): DRAM bytes (`traffic_bytes_per_launch`)
+    and L2 bytes (`l2_bytes_per_launch`), or None when the summary was taken
+    from other kernel source than the current one, or for a variant run."""
     if variant:
         return None
     path = os.path.join(ROOT, "profiles", f"walk_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
+    keys = ("traffic_bytes_per_launch", "l2_bytes_per_launch", "kernel_source_sha")
     for line in open(path):
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha")):
+        if ":" in line and line.strip().startswith(keys):
             k, v = line.strip().split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha") != kernel_source_sha():
         return None
-    try:
-        return float(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    out = {}
+    for k in ("traffic_bytes_per_launch", "l2_bytes_per_launch"):
+        try:
+            out[k] = float(vals[k])
+        except (KeyError, ValueError):
+            out[k] = None
+    return out
+
+
+def walk_roofline(tet_steps, rays, walk_ms, trace_ms, step_ms, hbm, hbm_src, l2_peak,
+                  record_bytes, prof, kind):
+    """The walk kernel's roofline for one step (two walk launches: primary
+    and secondary rays).  `frac` counts the method's algorithmic bytes (the
+    Tet16 record and the float4 point per tet step) over the walk's event
+    time against the measured HBM copy rate; `frac_trace` adds the per-ray
+    bytes over the whole trace (start, walk, finish).  The bytes the walk
+    fetches from DRAM and moves through L2 per launch (ncu, when the
+    committed summary matches this source) give `dram_frac` and `l2_frac`."""
+    alg = tet_steps * METHOD_STEP_BYTES
+    achieved = alg / (walk_ms * 1e-3) / 1e9
+    trace_alg = alg + rays * METHOD_RAY_BYTES
+    rec = tet_steps * record_bytes
+    walk_s_launch = walk_ms * 1e-3 / 2
+    traffic = prof.get("traffic_bytes_per_launch") if prof else None
+    l2b = prof.get("l2_bytes_per_launch") if prof else None
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": traffic,
+            "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
+            else "fallback 6.8 TB/s",
+            "kernel": f"walk_kernel (primary + {kind} launches; bytes and time per step)",
+            "bytes_per_tet_step": METHOD_STEP_BYTES,
+            "bytes_per_ray": METHOD_RAY_BYTES,
+            "algorithmic_bytes_per_launch": alg // 2,
+            "walk_ms_per_launch": round(walk_ms / 2, 4),
+            "tet_steps_per_step": tet_steps,
+            "frac_trace": round(trace_alg / (trace_ms * 1e-3) / 1e9 / hbm, 4),
+            "record_bytes_per_tet_step": record_bytes,
+            "frac_record_bytes": round(rec / (walk_ms * 1e-3) / 1e9 / hbm, 4),
+            "dram_frac": round(traffic / walk_s_launch / 1e9 / hbm, 4) if traffic else None,
+            "l2_bytes": l2b,
+            "l2_frac": round(l2b / walk_s_launch / 1e9 / l2_peak, 4) if l2b else None,
+            "l2_read_peak_gbs": round(l2_peak, 1),
+            "l2_peak_source": "measured here: a read probe (L1-bypassing 16-byte loads) over a "
+                              "48 MiB buffer resident in L2",
+            "walk_share_of_step": round(walk_ms / step_ms, 4),
+            "trace_share_of_step": round(trace_ms / step_ms, 4)}
 
 
 class ClockSampler:
@@ -295,13 +364,13 @@ def run_ours(args, world, rank, local):
         e.record(stream)                                  # materialise the CUDA events
     torch.cuda.synchronize()
 
-    def opts(mode, ev=None, secondary=False):
+    def opts(mode, ev=None, secondary=False, fmt=None):
         # early exit at t_max for the secondary rays with a finite t_max only
         # (primary rays are unbounded)
         bounded = secondary and W["tmax"] is not None and math.isfinite(W["tmax"])
         return tmx.trace_opts(mode=mode, block=args.block, refill=args.refill,
                               batch_steps=args.batch_steps, tmax_early_exit=bounded,
-                              phase_events=ev, format=args.format)
+                              phase_events=ev, format=fmt or args.format)
 
     def step(op, ob):
         mesh.locate(eye, out=start)
@@ -319,8 +388,8 @@ def run_ours(args, world, rank, local):
             mesh.gen_specular(rays, hits, kind, IOR, rays_out=rays2, count=count)
             mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
 
-    def timed(mode, steps, warmup):
-        op, ob = opts(mode, ev_p), opts(mode, ev_b, secondary=True)
+    def timed(mode, steps, warmup, fmt=None):
+        op, ob = opts(mode, ev_p, fmt=fmt), opts(mode, ev_b, secondary=True, fmt=fmt)
         for _ in range(warmup):
             step(op, ob)
         torch.cuda.synchronize()
@@ -346,21 +415,23 @@ def run_ours(args, world, rank, local):
         tot = max_over_ranks(tot, dev)                     # the slowest replica's time
         return tot / steps, trace_ms / steps, walk_ms / steps, launches
 
+    def capture():
+        """Host copies of the frame the last step traced: primary hits, the
+        rays generated from them, and their hits."""
+        k = int(count.item())
+        return dict(hits=hits.cpu().numpy(), rays2=rays2[:k].cpu().numpy(),
+                    hits2=hits2[:k].cpu().numpy())
+
     # headline arm: FP32 walk with FP64 guard
     with ClockSampler(local) as clk:
         ms, trace_ms, walk_ms, launches = timed("fp32g", args.steps, max(args.warmup, 3))
+    frames = {"fp32g": capture()}
     n_second = int(count.item())
     rays_per_step = n_primary + n_second
     g1 = tmx.unpack_hits(hits)
     g2 = tmx.unpack_hits(hits2[:n_second])
     steps_total = int(g1["steps"].astype(np.int64).sum() + g2["steps"].astype(np.int64).sum())
-    step_bytes = RECORD_BYTES[args.format] + POINT_BYTES.get(args.format, 16)
-    alg_bytes = steps_total * step_bytes + rays_per_step * WALK_RAY_BYTES
-    guard_rate = float(((g1["flags"] & tmx.HIT_GUARD) != 0).mean())
-    fl = np.concatenate([g1["flags"], g2["flags"]])
-    slow_rate = float(((fl & tmx.HIT_SLOW_PASS) != 0).mean())
-    retest_rate = float(((fl & tmx.HIT_GUARD) != 0).mean())
-    final64_rate = float(((np.concatenate([g1["flags"], g2["flags"]]) & tmx.HIT_FINAL_FP64) != 0).mean())
+    record_bytes = RECORD_BYTES[args.format] + POINT_BYTES.get(args.format, 16)
     value = world * rays_per_step / (ms * 1e-3) / 1e6
     extra = {}
     if kind == "shadow":
@@ -370,41 +441,44 @@ def run_ours(args, world, rank, local):
         extra = {"ior": IOR, "secondary_hit_rate": float((g2["tri"] >= 0).mean()) if n_second else 0.0}
 
     hbm, hbm_src = measured_hbm()
-    achieved = alg_bytes / (walk_ms * 1e-3) / 1e9
     l2_peak = measured_l2(torch, tmx, dev)
-    traffic = profiled_traffic(args.workload, "" if default_run else "variant")
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
-                else "fallback 6.8 TB/s",
-                "kernel": f"walk_kernel (primary + {kind} launches; bytes and time per step)",
-                "bytes_per_tet_step": step_bytes,
-                "algorithmic_bytes_per_launch": alg_bytes // 2,
-                "walk_ms_per_launch": round(walk_ms / 2, 4),
-                "tet_steps_per_step": steps_total,
-                "walk_share_of_step": round(walk_ms / ms, 4),
-                "l2_read_peak_gbs": round(l2_peak, 1),
-                "l2_peak_source": "measured here: the library's read probe (L1-bypassing 16-byte "
-                                  "loads) over a 48 MiB buffer resident in L2",
-                "frac_of_l2": round(achieved / l2_peak, 4),
-                "trace_share_of_step": round(trace_ms / ms, 4)}
+    prof = profiled_counters(args.workload, "" if default_run else "variant")
+    roofline = walk_roofline(steps_total, rays_per_step, walk_ms, trace_ms, ms, hbm, hbm_src,
+                             l2_peak, record_bytes, prof, kind)
 
     arms = {}
     if not args.no_arms:
-        keep = (hits.clone(), hits2.clone(), n_second)
-        for mode in ("fp64", "fp32"):
-            ams, atr, awk, _ = timed(mode, max(2, args.steps // 3), 1)
-            arms[mode] = {"value": round(world * (n_primary + int(count.item())) / (ams * 1e-3) / 1e6, 2),
+        keep = (hits.clone(), hits2.clone(), rays2.clone(), count.clone())
+        arm_list = [("fp64", args.format), ("fp32", args.format)]
+        if args.format != "tet16":
+            arm_list.append(("fp32g", "tet16"))   # the paper's compact record, same step
+        for mode, fmt in arm_list:
+            name = mode if fmt == args.format else fmt
+            ams, atr, awk, _ = timed(mode, max(2, args.steps // 3), 1, fmt=fmt)
+            frames[name] = capture()
+            k = int(count.item())
+            arms[name] = {"value": round(world * (n_primary + k) / (ams * 1e-3) / 1e6, 2),
                           "ms_per_step": round(ams, 3), "trace_ms": round(atr, 3),
-                          "walk_ms": round(awk, 3)}
-            if mode == "fp64":
-                a = tmx.unpack_hits(hits)
-                arms[mode]["primary_id_agreement_vs_fp32g"] = float((a["tri"] == g1["tri"]).mean())
-                both = (a["tri"] == g1["tri"]) & (a["tri"] >= 0)
-                rel = np.abs(g1["t"][both].astype(np.float64) - a["t"][both]) / np.abs(a["t"][both])
-                arms[mode]["primary_max_rel_t_fp32g_vs_fp64"] = float(rel.max()) if both.any() else 0.0
+                          "walk_ms": round(awk, 3), "mode": MODE_NAMES[mode], "format": fmt}
+            if fmt == "tet16":
+                a1, a2 = tmx.unpack_hits(hits), tmx.unpack_hits(hits2[:k])
+                st = int(a1["steps"].astype(np.int64).sum() + a2["steps"].astype(np.int64).sum())
+                arms[name]["roofline"] = walk_roofline(st, n_primary + k, awk, atr, ams, hbm, hbm_src,
+                                                       l2_peak, RECORD_BYTES["tet16"] + 16, None,
+                                                       kind)
         arms["fp32g_speedup_vs_fp64"] = round(value / arms["fp64"]["value"], 2)
-        hits.copy_(keep[0])
+        hits.copy_(keep[0]); hits2.copy_(keep[1]); rays2.copy_(keep[2]); count.copy_(keep[3])
+
+    info = mesh.info
+    nt = s.n_tets
+    face_bytes = {"face16": 64, "face": 128}.get(args.format, 0) * nt
+    memory = {"device_bytes": int(info.device_bytes),
+              "device_bytes_per_tet": round(info.device_bytes / nt, 2),
+              "walk_record_bytes_per_tet": {"tet16": 16, "tet20": 20, "tet20_aos": 20, "tet32": 32,
+                                            "face": 128, "face16": 64}[args.format],
+              "device_bytes_per_tet_without_face_entries": round((info.device_bytes - face_bytes) / nt, 2),
+              "note": "per tet: 16 B Tet16 + 32 B cold record (start phase) + face entries when "
+                      "the walk reads them; points, triangle and restart records spread over the tets"}
 
     e2e = None
     if not args.no_e2e and kind in ("bounce", "ao"):
@@ -412,10 +486,16 @@ def run_ours(args, world, rank, local):
                       fmt=args.format)
 
     cpu = None
+    vs_oracle = None
     if not args.no_cpu and world == 1 and rank == 0 and kind in ("bounce", "ao"):
-        cpu = cpu_baseline(args.workload, s, W, budget_s=20.0)
+        cpu, vs_oracle = oracle_leg(args.workload, s, W, frames, tmx, budget_s=20.0)
 
     if rank == 0:
+        fl1, fl2 = g1["flags"], g2["flags"]
+        fl = np.concatenate([fl1, fl2])
+
+        def rate(a, bit):
+            return float(((a & bit) != 0).mean()) if len(a) else 0.0
         metric = METRIC if kind == WORKLOADS[args.workload]["kind"] else f"Mrays/s (primary + {kind})"
         line = {
             "metric": metric, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -425,15 +505,21 @@ def run_ours(args, world, rank, local):
             "config": {"workload": f"{args.workload}: {W['desc']}", "mode": "FP32 walk + FP64 guard",
                        "tets": s.n_tets, "points": s.n_points, "triangles": s.n_tris,
                        "rays_per_step": rays_per_step, "primary": n_primary, "secondary": n_second,
-                       "order": args.order, "format": args.format, "secondary": kind,
+                       "order": args.order, "format": args.format, "secondary_kind": kind,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between steps (256 MiB write outside the step events)",
-                       "build_s": round(build_s, 2),
-                       "guard_rate_primary": guard_rate, "guard_rate_all": retest_rate,
-                       "parked_rate": slow_rate,
-                       "final_fp64_rate": final64_rate, **extra},
-            "roofline": roofline, "arms": arms, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "cpu_baseline": cpu,
+                       "build_s": round(build_s, 2), **extra},
+            # how often each double-precision path ran (fraction of the step's rays)
+            "fp64_paths": {"guard_rate_primary": rate(fl1, tmx.HIT_GUARD),
+                           "guard_rate_all": rate(fl, tmx.HIT_GUARD),
+                           "final_fp64_rate": rate(fl, tmx.HIT_FINAL_FP64),
+                           "restart_3d_rate": rate(fl2, tmx.HIT_RESTART_3D),
+                           "start_moved_rate": rate(fl, tmx.HIT_START_MOVED),
+                           "parked_rate": rate(fl, tmx.HIT_SLOW_PASS),
+                           "tie_rate": rate(fl, tmx.HIT_TIE),
+                           "bad_start_rate": rate(fl, tmx.HIT_BAD_START)},
+            "roofline": roofline, "arms": arms, "memory": memory, "vs_oracle": vs_oracle,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -560,6 +646,58 @@ def oracle_step(om, s, W, cam_tet, sel, nthreads, brute=False):
     return len(o) + len(o2)
 
 
+def oracle_leg(workload, s, W, frames, tmx, budget_s=20.0):
+    """The oracle on the host, after the timed GPU work: its rate on a
+    bounded sample (cpu_baseline), then every GPU arm's frame against it
+    (vs_oracle).  The rays each arm traced are given to the oracle as they
+    are: the primary rays of the camera, and the secondary rays the device
+    generated from that arm's own hits, each started from its restart face.
+    Where the tet adjacency is too large for the host (the large scene), the
+    oracle's brute force over all triangles checks an evenly spaced sample."""
+    import oracle
+    import scenegen as sg
+    from oracle.parity import meets_bar, stats
+    nthreads = oracle.default_threads()
+    big = s.n_tets > 20_000_000
+    om = oracle.OracleTriangles(s.points, s.tris) if big else oracle.OracleMesh(s.points, s.tets, s.tris)
+    cpu = cpu_baseline(workload, s, W, budget_s=budget_s, om=om)
+    t0 = time.time()
+    o, d = sg.camera_rays(s.camera)
+    n = len(o)
+    if big:
+        sel = np.arange(0, n, max(1, n // 2000))
+        w1 = om.bruteforce(o[sel], d[sel], np.inf, nthreads=nthreads)
+    else:
+        sel = np.arange(n)
+        cam_tet, _ = om.locate(np.array([s.camera.eye], np.float32), nthreads=nthreads)
+        w1 = om.trace(o, d, np.inf, cam_tet[0], nthreads=nthreads)
+    out = {}
+    for arm, fr in frames.items():
+        g1 = tmx.unpack_hits(fr["hits"][sel])
+        r2 = fr["rays2"]
+        sel2 = np.arange(0, len(r2), max(1, len(r2) // 4000)) if big else np.arange(len(r2))
+        r2 = r2[sel2]
+        g2 = tmx.unpack_hits(fr["hits2"][sel2])
+        entry = -1 - r2.view(np.int32)[:, 3]
+        if big:
+            w2 = om.bruteforce(r2[:, 0:3], r2[:, 4:7], r2[:, 7], exclude=entry >> 1,
+                               nthreads=nthreads)
+        else:
+            w2 = om.trace(r2[:, 0:3], r2[:, 4:7], r2[:, 7], -1, entry, nthreads=nthreads)
+        sp, ss = stats(s.points, s.tris, g1, w1), stats(s.points, s.tris, g2, w2)
+        out[arm] = {"primary": sp, "secondary": ss, "meets_bar": meets_bar(sp) and meets_bar(ss),
+                    "t_within_1e-5": sp["max_rel_t"] <= 1e-5 and ss["max_rel_t"] <= 1e-5}
+    out["sample"] = ("every ray of the frame (primary rays and each arm's device-generated "
+                     f"{W['kind']} rays), FP64 face-plane walk"
+                     if not big else
+                     f"every {max(1, n // 2000)}th primary ray and an even sample of about 4000 "
+                     f"{W['kind']} rays per arm, FP64 brute force over all {s.n_tris} triangles")
+    out["bar"] = ("ids identical for >= 99.999 % of rays, every mismatch within 1e-6 of a "
+                  "triangle edge; t within 1e-5 relative")
+    out["oracle_s"] = round(time.time() - t0, 1)
+    return cpu, out
+
+
 def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
     import oracle
     nthreads = oracle.default_threads()
@@ -567,7 +705,8 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
     # scene) takes the oracle's brute force over all triangles instead
     big = s.n_tets > 20_000_000
     if big:
-        om = oracle.OracleTriangles(s.points, s.tris)
+        if om is None:
+            om = oracle.OracleTriangles(s.points, s.tris)
         cam_tet = [-1]
     else:
         if om is None:

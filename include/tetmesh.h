@@ -418,13 +418,6 @@ void tm_batch_destroy(tm_batch *b);
  * these keys on a 2^21 grid over the bounding cube. */
 tm_status tm_hilbert_keys(const uint32_t *ijk, int64_t n, int bits, uint64_t *keys);
 
-/* Measurement helper, not part of the method: reads `bytes` (a multiple of
- * 16) of DEVICE memory at buf (16-byte aligned) `reps` times on `stream`
- * with L1-bypassing loads, one kernel per pass; *sink (DEVICE int32) may
- * receive a checksum.  Timed by the caller, it gives the read bandwidth of
- * L2 (a buffer that fits in it) or of HBM (a larger one). */
-tm_status tm_read_probe(const void *buf, int64_t bytes, int reps, int32_t *sink, void *stream);
-
 /* Text of a status; text of the last CUDA error seen by this thread. */
 const char *tm_status_str(tm_status s);
 const char *tm_last_error(void);

@@ -78,7 +78,6 @@ _SIGS = {
     "tm_mesh_export_faces": ([P, P], ctypes.c_int),
     "tm_mesh_export_faces16": ([P, P], ctypes.c_int),
     "tm_mesh_export_restart": ([P, P], ctypes.c_int),
-    "tm_read_probe": ([P, i64, ctypes.c_int, P, P], ctypes.c_int),
     "tm_map_ids": ([P, ctypes.c_int, ctypes.c_int, P, P, i64], ctypes.c_int),
     "tm_hilbert_keys": ([P, i64, ctypes.c_int, P], ctypes.c_int),
     "tm_locate": ([P, P, i64, P, i32, P, P], ctypes.c_int),

@@ -17,7 +17,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtetmesh.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["trace.cu", "locate.cu", "raygen.cu", "batch.cu", "probe.cu", "build.cpp", "capi.cpp"]
+SOURCES = ["trace.cu", "locate.cu", "raygen.cu", "batch.cu", "build.cpp", "capi.cpp"]
+# The benchmark's read-bandwidth probe: a library of its own, outside the C ABI.
+PROBE_SOURCE = "bench_probe.cu"
+PROBE_LIB = os.path.join(BUILD, "libtmprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3",
           f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
@@ -40,9 +43,9 @@ def _compile(src: str, extra: list[str]) -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
         os.path.join(ROOT, "include", "tetmesh.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
@@ -54,14 +57,15 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES + [PROBE_SOURCE]))
+    for out, parts in ((LIB, objs[:-1]), (PROBE_LIB, objs[-1:])):
+        tmp = out + ".tmp"
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *parts, "-Xcompiler", "-fopenmp", "-lgomp"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

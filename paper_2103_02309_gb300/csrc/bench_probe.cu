@@ -1,9 +1,12 @@
-// Read-bandwidth probe for the benchmark's rooflines (a measurement helper,
-// not part of the traversal): every thread streams 64 bytes per iteration
-// with L1-bypassing 16-byte loads over a caller buffer, so a buffer that fits
-// in L2 measures the L2 read bandwidth, one larger than L2 the HBM read
+// Read-bandwidth probe for the benchmark's rooflines.  A measurement helper,
+// not part of the traversal and not part of the library's C ABI: it is
+// built into its own small library (libtmprobe.so), which only the
+// benchmark loads.  Every thread streams 64 bytes per iteration with
+// L1-bypassing 16-byte loads over a caller buffer, so a buffer that fits in
+// L2 measures the L2 read bandwidth, one larger than L2 the HBM read
 // bandwidth.
-#include "tm_internal.h"
+#include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace {
 
@@ -26,13 +29,18 @@ read_probe_kernel(const int4 *__restrict__ p, int64_t n16, int32_t *__restrict__
 
 }  // namespace
 
-extern "C" tm_status tm_read_probe(const void *buf, int64_t bytes, int reps, int32_t *sink,
+// Reads `bytes` (a multiple of 16) of DEVICE memory at buf (16-byte aligned)
+// `reps` times on `stream`, one kernel per pass; *sink (DEVICE int32) may
+// receive a checksum.  Returns 0, 1 for a bad argument, or 2 when a CUDA
+// call failed.
+extern "C" int tm_bench_read_probe(const void *buf, int64_t bytes, int reps, int32_t *sink,
                                    void *stream) {
     if (!buf || !sink || bytes <= 0 || (bytes & 15) || (((uintptr_t)buf) & 15u) || reps < 1)
-        return TM_ERR_ARG;
+        return 1;
     int dev = 0, sms = 0;
-    TM_CUDA(cudaGetDevice(&dev));
-    TM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 2;
     const int64_t n16 = bytes / 16;
     int64_t grid = (int64_t)sms * 8;
     const int64_t need = (n16 + 255) / 256;
@@ -40,11 +48,5 @@ extern "C" tm_status tm_read_probe(const void *buf, int64_t bytes, int reps, int
     for (int r = 0; r < reps; ++r)
         read_probe_kernel<<<(int)grid, 256, 0, (cudaStream_t)stream>>>(
             static_cast<const int4 *>(buf), n16, sink);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        tm_set_error("read_probe launch", e);
-        return TM_ERR_CUDA;
-    }
-    tm_count_launches((uint64_t)reps);
-    return TM_OK;
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

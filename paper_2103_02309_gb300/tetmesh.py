@@ -306,12 +306,6 @@ def hilbert_keys(ijk, bits: int) -> np.ndarray:
     return out
 
 
-def read_probe(buf: torch.Tensor, reps: int, sink: torch.Tensor, stream=None) -> None:
-    """Read `buf` (device, contiguous) `reps` times (bandwidth probe)."""
-    N.check(N.lib.tm_read_probe(_dptr(buf), buf.numel() * buf.element_size(), int(reps),
-                                _dptr(sink), _stream(stream)), "tm_read_probe")
-
-
 def launch_count() -> int:
     return int(N.lib.tm_launch_count())
 

@@ -8,7 +8,8 @@ The tet adjacency of this mesh is too large to build on the host in a test,
 so the expected hits come from the oracle's brute force over all triangles
 (the plain definition of the hit) on sampled rays; the side each ray arrives
 from is taken from the geometry.  The device-generated occlusion rays of the
-whole frame are checked by properties that hold at any size.
+whole frame are checked by properties that hold at any size, and an even
+sample of them by the brute force.
 """
 from types import SimpleNamespace
 
@@ -57,7 +58,7 @@ def large(tmx):
                                        np.float32(w["b2"][k]), side, AO_SEED, AO_PER_HIT, AO_TMAX,
                                        ray_ids=sel[k])
     wb = ts.bruteforce(ob, db, tb, exclude=eb >> 1)
-    return SimpleNamespace(s=s, mesh=mesh, sel=sel, w=w, ao=(ob, db, tb, eb), wb=wb)
+    return SimpleNamespace(s=s, mesh=mesh, ts=ts, sel=sel, w=w, ao=(ob, db, tb, eb), wb=wb)
 
 
 @pytest.mark.parametrize("mode", ["fp32g", "fp64"])
@@ -100,4 +101,12 @@ def test_large_full_size_sampled(tmx, large, mode):
     assert np.linalg.norm(on_ray - on_tri, axis=1).max() < 4e-6
     assert (g2["b1"][hit] >= -1e-5).all() and (g2["b2"][hit] >= -1e-5).all()
     assert (g2["b1"][hit] + g2["b2"][hit] <= 1 + 1e-5).all()
-    print(mode, "primary", st, "ao", st2)
+    # and an even sample of them against the oracle's brute force, each from
+    # its restart face
+    pick = np.sort(sel2)[:: max(1, len(sel2) // 3000)]
+    rp = r2[torch.from_numpy(pick).cuda()].cpu().numpy()
+    gp = tmx.unpack_hits(h2[torch.from_numpy(pick).cuda()])
+    ep = -1 - rp.view(np.int32)[:, 3]
+    wp = L.ts.bruteforce(rp[:, 0:3], rp[:, 4:7], rp[:, 7], exclude=ep >> 1)
+    st3 = compare(L.s.points, L.s.tris, gp, wp)
+    print(mode, "primary", st, "ao", st2, "device ao", st3)

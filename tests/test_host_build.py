@@ -39,6 +39,17 @@ def test_library_exports_every_declared_symbol(tmx):
     assert set(N.EXPORTED) <= set(declared)
 
 
+def test_bench_probe_is_a_library_of_its_own(tmx):
+    """The benchmark's read-bandwidth probe is outside the C ABI: its own
+    library exports it, the traversal library does not."""
+    import ctypes
+    from paper_2103_02309_gb300 import _native as N
+    from paper_2103_02309_gb300 import build as libbuild
+    assert not hasattr(N.lib, "tm_read_probe") and not hasattr(N.lib, "tm_bench_read_probe")
+    probe = ctypes.CDLL(libbuild.PROBE_LIB)
+    assert hasattr(probe, "tm_bench_read_probe")
+
+
 def expected_raw_neighbours(om, tinv):
     """Neighbour field values the packing must produce, per (input tet, local face)."""
     nbr, fc, _ = om.arrays()
