@@ -110,6 +110,13 @@ def parse():
                         "library's automatic choice when built)")
     p.add_argument("--secondary", choices=sorted(SECONDARY), default=None,
                    help="rays generated from the primary hits (default: the workload's)")
+    p.add_argument("--split", choices=["replicas", "tiles"], default="replicas",
+                   help="with N ranks: every rank traces a whole frame of its own (replicas, "
+                        "weak scaling), or the ranks split one frame by pixel tiles and gather "
+                        "its hits to rank 0 inside the timed step (tiles, strong scaling)")
+    p.add_argument("--cells", type=int, default=0,
+                   help="grid cells per axis instead of the workload's (a reduced case of the "
+                        "same scene recipe, e.g. for counter captures)")
     p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
@@ -305,9 +312,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_scene(workload):
+def build_scene(workload, cells=0):
     import scenegen as sg
-    return sg.make_config(workload)
+    return sg.make_config(workload, n_override=cells or None)
 
 
 # --------------------------------------------------------------------------- #
@@ -324,7 +331,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     from paper_2103_02309_gb300 import tetmesh as tmx
-    from paper_2103_02309_gb300.shard import max_over_ranks
+    from paper_2103_02309_gb300.shard import gather_rows, max_over_ranks, shard_seed, tile_range
 
     W = dict(WORKLOADS[args.workload])
     if args.format is None:
@@ -333,7 +340,7 @@ def run_ours(args, world, rank, local):
     if kind != W["kind"]:
         W["per_hit"], W["tmax"] = SECONDARY[kind]
         W["kind"] = kind
-    s = build_scene(args.workload)
+    s = build_scene(args.workload, args.cells)
     t0 = time.time()
     mesh = tmx.Mesh(s.points, s.tets, s.tris, order=args.order,
                     tet20=args.format.startswith("tet20"), faces=args.format == "face",
@@ -344,7 +351,12 @@ def run_ours(args, world, rank, local):
     per_hit = W["per_hit"]
     default_run = (kind == WORKLOADS[args.workload]["kind"]
                    and args.format == WORKLOADS[args.workload].get("format", "face16")
-                   and args.order == "hilbert")
+                   and args.order == "hilbert" and not args.cells)
+    # one frame split by pixel tiles: this rank's rays [lo, hi), and the seed
+    # that gives its secondary rays the whole frame's random draws
+    tiles = args.split == "tiles"
+    lo, hi = tile_range(n_primary, world, rank) if tiles else (0, n_primary)
+    seed2 = shard_seed(0x5EED, lo, per_hit) if tiles else 0x5EED
     dev = torch.device("cuda", local)
     eye = torch.tensor([s.camera.eye], dtype=torch.float32, device=dev)
     start = torch.empty(1, dtype=torch.int32, device=dev)
@@ -372,21 +384,27 @@ def run_ours(args, world, rank, local):
                               batch_steps=args.batch_steps, tmax_early_exit=bounded,
                               phase_events=ev, format=fmt or args.format)
 
+    r1, h1 = rays[lo:hi], hits[lo:hi]                     # the whole frame unless split by tiles
+
     def step(op, ob):
         mesh.locate(eye, out=start)
         if kind == "shadow":
             mesh.locate(light, out=light_tet)          # the point light, once per frame
         tmx.gen_primary(cam, start, rays=rays)
-        mesh.trace(rays, hits=hits, opts=op)
+        mesh.trace(r1, hits=h1, opts=op)
         if kind in ("bounce", "ao"):
-            mesh.gen_secondary(hits, per_hit, W["tmax"], seed=0x5EED, rays_out=rays2, count=count)
+            mesh.gen_secondary(h1, per_hit, W["tmax"], seed=seed2, rays_out=rays2, count=count)
             mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
         elif kind == "shadow":
-            mesh.gen_shadow(hits, LIGHT, rays_out=rays2, count=count)
+            mesh.gen_shadow(h1, LIGHT, rays_out=rays2, count=count)
             mesh.trace_shadow(rays2, light_tet, hits=hits2, n_dev=count, opts=ob)
         else:
-            mesh.gen_specular(rays, hits, kind, IOR, rays_out=rays2, count=count)
+            mesh.gen_specular(r1, h1, kind, IOR, rays_out=rays2, count=count)
             mesh.trace(rays2, hits=hits2, n_dev=count, opts=ob)
+        if tiles and world > 1:
+            # rank 0 collects the frame's hits in pixel-tile order
+            gather_rows(h1, world, rank, device=dev)
+            gather_rows(hits2[: int(count.item())], world, rank, device=dev)
 
     def timed(mode, steps, warmup, fmt=None):
         op, ob = opts(mode, ev_p, fmt=fmt), opts(mode, ev_b, secondary=True, fmt=fmt)
@@ -427,12 +445,18 @@ def run_ours(args, world, rank, local):
         ms, trace_ms, walk_ms, launches = timed("fp32g", args.steps, max(args.warmup, 3))
     frames = {"fp32g": capture()}
     n_second = int(count.item())
-    rays_per_step = n_primary + n_second
+    if tiles and world > 1:
+        import torch.distributed as dist
+        tot = torch.tensor([n_second], dtype=torch.int64, device=dev)
+        dist.all_reduce(tot)
+        rays_per_step = n_primary + int(tot.item())   # the frame's rays, over all ranks
+    else:
+        rays_per_step = n_primary + n_second
     g1 = tmx.unpack_hits(hits)
     g2 = tmx.unpack_hits(hits2[:n_second])
     steps_total = int(g1["steps"].astype(np.int64).sum() + g2["steps"].astype(np.int64).sum())
     record_bytes = RECORD_BYTES[args.format] + POINT_BYTES.get(args.format, 16)
-    value = world * rays_per_step / (ms * 1e-3) / 1e6
+    value = (1 if tiles else world) * rays_per_step / (ms * 1e-3) / 1e6
     extra = {}
     if kind == "shadow":
         extra = {"light": LIGHT, "light_tet": int(light_tet.item()),
@@ -500,13 +524,18 @@ def run_ours(args, world, rank, local):
         line = {
             "metric": metric, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {W['desc']}", "mode": "FP32 walk + FP64 guard",
+            "higher_is_better": True, "scaling": "strong" if tiles else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {W['desc']}"
+                       + (f" (reduced to {args.cells}^3 cells)" if args.cells else ""),
+                       "mode": "FP32 walk + FP64 guard",
                        "tets": s.n_tets, "points": s.n_points, "triangles": s.n_tris,
                        "rays_per_step": rays_per_step, "primary": n_primary, "secondary": n_second,
                        "order": args.order, "format": args.format, "secondary_kind": kind,
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "parallelism": (f"one frame split by pixel tiles over {world} ranks, "
+                                       "hits gathered to rank 0" if tiles and world > 1
+                                       else f"replicas x{world}" if world > 1 else "1 GPU"),
+                       "rays_this_rank": [lo, hi],
                        "l2": "flushed between steps (256 MiB write outside the step events)",
                        "build_s": round(build_s, 2), **extra},
             # how often each double-precision path ran (fraction of the step's rays)
