@@ -117,6 +117,9 @@ def parse():
     p.add_argument("--cells", type=int, default=0,
                    help="grid cells per axis instead of the workload's (a reduced case of the "
                         "same scene recipe, e.g. for counter captures)")
+    p.add_argument("--eager", action="store_true",
+                   help="time the step as separate API calls instead of replaying it from a "
+                        "CUDA graph captured from the same calls")
     p.add_argument("--no-arms", action="store_true", help="skip the FP64 / FP32 comparison arms")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
@@ -376,7 +379,7 @@ def run_ours(args, world, rank, local):
         e.record(stream)                                  # materialise the CUDA events
     torch.cuda.synchronize()
 
-    def opts(mode, ev=None, secondary=False, fmt=None):
+    def opts(mode, ev=None, secondary=False, fmt=None):  # ev=None: no phase events (graph capture)
         # early exit at t_max for the secondary rays with a finite t_max only
         # (primary rays are unbounded)
         bounded = secondary and W["tmax"] is not None and math.isfinite(W["tmax"])
@@ -406,32 +409,68 @@ def run_ours(args, world, rank, local):
             gather_rows(h1, world, rank, device=dev)
             gather_rows(hits2[: int(count.item())], world, rank, device=dev)
 
+    # A step replays from a CUDA graph captured from the same API calls
+    # (one launch of the whole step instead of about thirty host calls),
+    # except for the tile split across ranks, whose gather synchronises with
+    # the host.  Phase times come from eager steps with the phase events.
+    use_graph = not args.eager and not (tiles and world > 1)
+
     def timed(mode, steps, warmup, fmt=None):
         op, ob = opts(mode, ev_p, fmt=fmt), opts(mode, ev_b, secondary=True, fmt=fmt)
         for _ in range(warmup):
             step(op, ob)
         torch.cuda.synchronize()
+        # phase times (start, walk, finish of both launches) from eager steps
+        n_phase = min(steps, 5)
+        phases = np.zeros((2, 3))                           # [primary, secondary] x [start, walk, finish]
+        trace_ms = walk_ms = 0.0
+        per_step = 0
+        for _ in range(n_phase):
+            flush.zero_()
+            l0 = tmx.launch_count()
+            step(op, ob)
+            torch.cuda.synchronize()
+            per_step = tmx.launch_count() - l0
+            trace_ms += ev_p[0].elapsed_time(ev_p[3]) + ev_b[0].elapsed_time(ev_b[3])
+            walk_ms += ev_p[1].elapsed_time(ev_p[2]) + ev_b[1].elapsed_time(ev_b[2])
+            for i, ev in enumerate((ev_p, ev_b)):
+                for j in range(3):
+                    phases[i, j] += ev[j].elapsed_time(ev[j + 1])
+        timed.phases = (phases / n_phase).round(4).tolist()
+        run = lambda: step(op, ob)  # noqa: E731
+        if use_graph:
+            g = torch.cuda.CUDAGraph()
+            opg, obg = opts(mode, fmt=fmt), opts(mode, secondary=True, fmt=fmt)
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                step(opg, obg)
+            stream.wait_stream(side)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                step(opg, obg)
+            g.replay()
+            torch.cuda.synchronize()
+            run = g.replay
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         l0 = tmx.launch_count()
-        tot, trace_ms, walk_ms = 0.0, 0.0, 0.0
+        tot = 0.0
         for _ in range(steps):
             flush.zero_()                                  # evict the mesh from L2 between steps
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(op, ob)
+            run()
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-            trace_ms += ev_p[0].elapsed_time(ev_p[3]) + ev_b[0].elapsed_time(ev_b[3])
-            walk_ms += ev_p[1].elapsed_time(ev_p[2]) + ev_b[1].elapsed_time(ev_b[2])
         torch.cuda.synchronize()
-        launches = tmx.launch_count() - l0
+        launches = per_step * steps if use_graph else tmx.launch_count() - l0
         if world > 1:
             torch.distributed.barrier()
         tot = max_over_ranks(tot, dev)                     # the slowest replica's time
-        return tot / steps, trace_ms / steps, walk_ms / steps, launches
+        return tot / steps, trace_ms / n_phase, walk_ms / n_phase, launches
 
     def capture():
         """Host copies of the frame the last step traced: primary hits, the
@@ -444,6 +483,9 @@ def run_ours(args, world, rank, local):
     with ClockSampler(local) as clk:
         ms, trace_ms, walk_ms, launches = timed("fp32g", args.steps, max(args.warmup, 3))
     frames = {"fp32g": capture()}
+    phase_ms = {"primary": dict(zip(("start", "walk", "finish"), timed.phases[0])),
+                "secondary": dict(zip(("start", "walk", "finish"), timed.phases[1])),
+                "note": "event-timed per launch; start includes the ordering passes of the pool"}
     n_second = int(count.item())
     if tiles and world > 1:
         import torch.distributed as dist
@@ -537,6 +579,9 @@ def run_ours(args, world, rank, local):
                                        else f"replicas x{world}" if world > 1 else "1 GPU"),
                        "rays_this_rank": [lo, hi],
                        "l2": "flushed between steps (256 MiB write outside the step events)",
+                       "launch": ("each step replayed from a CUDA graph captured from the API calls; "
+                                  "phase times from eager steps") if use_graph else
+                                 "each step as separate API calls",
                        "build_s": round(build_s, 2), **extra},
             # how often each double-precision path ran (fraction of the step's rays)
             "fp64_paths": {"guard_rate_primary": rate(fl1, tmx.HIT_GUARD),
@@ -547,7 +592,8 @@ def run_ours(args, world, rank, local):
                            "parked_rate": rate(fl, tmx.HIT_SLOW_PASS),
                            "tie_rate": rate(fl, tmx.HIT_TIE),
                            "bad_start_rate": rate(fl, tmx.HIT_BAD_START)},
-            "roofline": roofline, "arms": arms, "memory": memory, "vs_oracle": vs_oracle,
+            "roofline": roofline, "phase_ms": phase_ms, "arms": arms, "memory": memory,
+            "vs_oracle": vs_oracle,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

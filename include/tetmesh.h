@@ -322,10 +322,15 @@ tm_status tm_gen_primary(const tm_camera *cam, const int32_t *start_dev, float t
  * DEVICE hits, `per_hit` rays leave the hit triangle back into the arrival
  * side's tet, with cosine-weighted directions about the triangle normal and
  * the given tmax.  Random numbers: SplitMix64 as a counter-based generator,
- * draw 2*(i*per_hit + k) + j of stream `seed`.  Output is compacted in hit
- * order into DEVICE rays_out (capacity n*per_hit), the count is written to
- * DEVICE *count_dev (int64), and src_out (DEVICE int32, may be NULL) gets the
- * index i of each ray's hit.  hits may hold n_dev (DEVICE int64, may be
+ * draw 2*(i*per_hit + k) + j of stream `seed`.  Output is compacted into
+ * DEVICE rays_out (capacity n*per_hit) in 8 groups by the length of the
+ * longest walk the hit's first ray can make (to the mesh's bounding box, or
+ * to tmax), longest first, so that a walk over them takes its long rays
+ * early and ends with a shorter tail; within a group the hits keep their
+ * order, and the per_hit rays of one hit are consecutive.  The order does
+ * not depend on scheduling.  The count is written to DEVICE *count_dev
+ * (int64), and src_out (DEVICE int32, may be NULL) gets the index i of each
+ * ray's hit.  hits may hold n_dev (DEVICE int64, may be
  * NULL) valid entries instead of n.  A hit whose cface is not a constrained
  * face of this mesh (0 <= cface < n_tris fails: a foreign or corrupted
  * record) counts as a miss here and in the other generators. */
@@ -338,9 +343,9 @@ tm_status tm_gen_secondary(const tm_mesh *mesh, const tm_hit *hits, int64_t n,
  * (triangle (a, b, c) in input order, float32) toward the point light
  * (lx, ly, lz): d = (L - x) / |L - x|, tmax = |L - x|, restarted from the
  * hit triangle into its side that faces the light (the + side when
- * ((b - a) x (c - a)) . (L - a) >= 0).  Output, compaction, count and
- * src_out as tm_gen_secondary (capacity n).  Trace them with
- * tm_trace_shadow. */
+ * ((b - a) x (c - a)) . (L - a) >= 0).  Output compacted in hit order
+ * (capacity n); count, src_out and n_dev as tm_gen_secondary.  Trace them
+ * with tm_trace_shadow. */
 tm_status tm_gen_shadow(const tm_mesh *mesh, const tm_hit *hits, int64_t n, const int64_t *n_dev,
                         float lx, float ly, float lz, tm_ray *rays_out, int64_t *count_dev,
                         int32_t *src_out, void *stream);
@@ -358,8 +363,8 @@ tm_status tm_gen_shadow(const tm_mesh *mesh, const tm_hit *hits, int64_t n, cons
  * toward the arrival side, c = -w . n_a (clamped at 0), and eta the ratio of
  * refractive indices (arrival side over far side): ior for rays arriving
  * from the - side, 1/ior from the + side (ior = index of the - side over
- * that of the + side).  Output, compaction, count and src_out as
- * tm_gen_secondary (capacity n), all rays with the given tmax. */
+ * that of the + side).  Output compacted in hit order (capacity n); count,
+ * src_out and n_dev as tm_gen_secondary; all rays with the given tmax. */
 enum { TM_SPECULAR_REFLECT = 0, TM_SPECULAR_REFRACT = 1 };
 tm_status tm_gen_specular(const tm_mesh *mesh, const tm_ray *rays_in, const tm_hit *hits,
                           int64_t n, const int64_t *n_dev, int kind, float ior, float tmax,
@@ -371,7 +376,7 @@ tm_status tm_gen_specular(const tm_mesh *mesh, const tm_ray *rays_in, const tm_h
  * has no counterpart: this is a property of the library, not of the method.
  * It calls no cudaMalloc, cudaFree or allocating library routine: its scan
  * scratch is a static device array of this library, sized for at most
- * TM_NOALLOC_MAX_HITS hits (about 192 KiB, held on every device that loads
+ * TM_NOALLOC_MAX_HITS hits (about 1.5 MiB, held on every device that loads
  * the library until the process exits).  n > TM_NOALLOC_MAX_HITS returns
  * TM_ERR_TOO_LARGE (tm_last_error() says why) and launches nothing.
  * The first call on each device looks up the array's device address and

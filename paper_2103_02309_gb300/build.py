@@ -35,7 +35,9 @@ def nvcc() -> str:
 
 def _compile(src: str, extra: list[str]) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    # TM_NVCC_DEFINES: extra -D options for the library's tuning macros
+    defines = os.environ.get("TM_NVCC_DEFINES", "").split()
+    cmd = [nvcc(), *ARCH, *COMMON, *defines, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")

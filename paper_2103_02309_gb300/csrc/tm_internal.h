@@ -75,6 +75,7 @@ struct MeshView {
     const int4 *face;      // face entries, two int4 each, four per tet (may be null)
     const int4 *face16;    // 16-byte face entries, four per tet (may be null)
     float lo[3], cell_inv;  // lattice origin and kSeedGrid / extent
+    float hi[3];            // the points' bounding box is [lo, hi]
 };
 
 inline MeshView mesh_view(const tm_mesh *m) {
@@ -95,7 +96,10 @@ inline MeshView mesh_view(const tm_mesh *m) {
     v.t20aos = m->d_t20aos;
     v.face = m->d_face;
     v.face16 = m->d_face16;
-    for (int a = 0; a < 3; ++a) v.lo[a] = m->lo[a];
+    for (int a = 0; a < 3; ++a) {
+        v.lo[a] = m->lo[a];
+        v.hi[a] = m->hi[a];
+    }
     v.cell_inv = m->extent > 0 ? (float)(kSeedGrid / m->extent) : 0.f;
     return v;
 }

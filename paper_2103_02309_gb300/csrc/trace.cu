@@ -42,7 +42,6 @@
 // re-test.  The hit slot (32 bytes per ray) carries the state between the
 // phases, so no scratch memory is needed beyond the cursor.
 #include <cmath>
-#include <mutex>
 
 #include "walk.cuh"
 
@@ -90,60 +89,13 @@ __device__ __forceinline__ Slot find_slot(const BatchDesc *d, int n_meshes, unsi
     return Slot{lo, (int32_t)(r - (unsigned long long)d[lo].offset)};
 }
 
-template <class R, bool BOUNDED> struct Depth {
-    __device__ __forceinline__ void init(const float4 &, const float4 &) {}
-    __device__ __forceinline__ void set(int, const float4 &) {}
-    __device__ __forceinline__ bool far(const float4 &) const { return false; }
-    __device__ __forceinline__ void put(int, bool) {}
-    __device__ __forceinline__ bool beyond() const { return false; }
-};
-template <class R> struct Depth<R, true> {
-    // whether each entry-face vertex lies beyond t_max along the ray (bit k
-    // for slot k): three bits instead of three depths keep the bounded walk's
-    // state small
-    R dx, dy, dz, dod, zmax;
-    uint32_t bits;
-    __device__ __forceinline__ void init(const float4 &w0, const float4 &w1) {
-        dx = w1.x; dy = w1.y; dz = w1.z;
-        dod = rfma(dz, R(w0.z), rfma(dy, R(w0.y), rmul(dx, R(w0.x))));
-        zmax = R(w1.w) * rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
-        bits = 0;
-    }
-    __device__ __forceinline__ R depth(const float4 &p) const {
-        return rfma(dz, R(p.z), rfma(dy, R(p.y), rmul(dx, R(p.x)))) - dod;
-    }
-    __device__ __forceinline__ bool far(const float4 &p) const { return depth(p) > zmax; }
-    __device__ __forceinline__ void put(int slot, bool b) {
-        bits = (bits & ~(1u << slot)) | ((uint32_t)b << slot);
-    }
-    __device__ __forceinline__ void set(int slot, const float4 &p) { put(slot, far(p)); }
-    // the entry face of the next tet lies entirely beyond t_max
-    __device__ __forceinline__ bool beyond() const { return bits == 7u; }
-};
-
 struct PhaseParams {
     int64_t n_cap;
     const int64_t *n_dev;
     float tau_rel;             // sign-test guard threshold relative to the mesh extent
     const int32_t *stop_tet;   // point-light rays: DEVICE id of the light's tet, else null
     int slot_i3;               // walk record word 2 = the next tet's fourth vertex (face entries)
-    int4 *wsr;                 // walk start records (16-byte face entries, float32), else null
-    int bounded;               // the walk stops at t_max: so does the start phase
 };
-
-// Walk start record of the 16-byte face-entry walk in the float32 modes:
-// kWsrWords int4 per ray in scratch, written by the start phase, so that a
-// lane of the walk takes a ray with independent reads only (no point to
-// fetch, no basis to compute):
-//   q0 {next tet (-1: the ray ended in the start phase), packed ranks, steps, flags}
-//   q1 {u.x, u.y, u.z, po.x}   q2 {v.x, v.y, v.z, po.y}   (the scaled basis)
-//   q3 {p0.x, p0.y, p1.x, p1.y}   q4 {p2.x, p2.y, p3.x, p3.y}
-// p0..p2 are the next tet's entry face (counter-clockwise) and p3 its fourth
-// vertex, projected.  Packed ranks: byte k < 3 holds the rank of slot k's
-// vertex among the next tet's ids, byte 3 that of the fourth vertex; bit 7
-// of byte k is set when that vertex lies beyond t_max (bounded walks).
-constexpr int kWsrWords = 5;
-constexpr uint32_t kWsrRanks = 0x03030303u;
 
 // The light's tet of a shadow launch, or -1 (none, or not a tet of the mesh).
 __device__ __forceinline__ int32_t load_stop(const int32_t *p, int32_t nt) {
@@ -208,55 +160,9 @@ __device__ __noinline__ int32_t search_start(const MeshView mv, const tm_ray *rp
 }
 
 // Phase 1 for one ray.
-// The walk start record of a ray that walks on from tet T into `next`
-// (16-byte face entries; see kWsrWords): the exit face's entry gives the
-// next tet's fourth vertex and its rank, the ranks of the entry face's
-// vertices follow from their ids.  A bounded ray whose entry face lies
-// entirely beyond t_max ends in T here.
-__device__ __noinline__ void start_record_face16(const MeshView mv, const Basis<float> B,
-                                                 const WalkState<float> S, int32_t T,
-                                                 uint32_t next, uint32_t steps, uint32_t flags,
-                                                 const tm_ray *rp, bool bounded, tm_hit *hp,
-                                                 int4 *wq) {
-    const int4 f = __ldg(mv.face16 + 4 * (int64_t)T + S.xr);
-    const uint32_t enc = (uint32_t)f.x;
-    if ((enc & 0x1FFFFFFFu) != next || (enc & TM_CFACE_FLAG)) {  // not the neighbour the line init read
-        put_end(hp, T, TM_BOUNDARY, steps, flags | TM_HIT_BAD_ID);
-        wq[0] = make_int4(-1, 0, 0, 0);
-        return;
-    }
-    const uint32_t w = (enc >> 29) & 3u;
-    const uint32_t a0 = (S.i1 < S.i0) + (S.i2 < S.i0), a1 = (S.i0 < S.i1) + (S.i2 < S.i1),
-                   a2 = (S.i0 < S.i2) + (S.i1 < S.i2);
-    uint32_t packed = (a0 + (a0 >= w)) | ((a1 + (a1 >= w)) << 8) | ((a2 + (a2 >= w)) << 16) | (w << 24);
-    const float4 x3 = make_float4(__int_as_float(f.y), __int_as_float(f.z), __int_as_float(f.w), 0.f);
-    const P2<float> p3 = B.project(x3.x, x3.y, x3.z);
-    if (bounded) {
-        Depth<float, true> Z;
-        Z.init(__ldg(reinterpret_cast<const float4 *>(rp)), __ldg(reinterpret_cast<const float4 *>(rp) + 1));
-        const bool f0 = Z.far(__ldg(mv.pts + S.i0)), f1 = Z.far(__ldg(mv.pts + S.i1)),
-                   f2 = Z.far(__ldg(mv.pts + S.i2));
-        if (f0 && f1 && f2) {  // the segment ends in T
-            put_end(hp, T, TM_BOUNDARY, steps, flags);
-            wq[0] = make_int4(-1, 0, 0, 0);
-            return;
-        }
-        packed |= ((uint32_t)f0 << 7) | ((uint32_t)f1 << 15) | ((uint32_t)f2 << 23) |
-                  ((uint32_t)Z.far(x3) << 31);
-    }
-    wq[0] = make_int4((int)next, (int)packed, (int)steps, (int)flags);
-    wq[1] = make_int4(__float_as_int(B.ux), __float_as_int(B.uy), __float_as_int(B.uz), __float_as_int(B.pox));
-    wq[2] = make_int4(__float_as_int(B.vx), __float_as_int(B.vy), __float_as_int(B.vz), __float_as_int(B.poy));
-    wq[3] = make_int4(__float_as_int(S.p0.x), __float_as_int(S.p0.y), __float_as_int(S.p1.x),
-                      __float_as_int(S.p1.y));
-    wq[4] = make_int4(__float_as_int(S.p2.x), __float_as_int(S.p2.y), __float_as_int(p3.x),
-                      __float_as_int(p3.y));
-}
-
 template <int MODE>
 __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, tm_hit *hp,
-                                          float tau_rel, int32_t stop_tet, bool slot_i3,
-                                          int4 *wq = nullptr, bool bounded = false) {
+                                          float tau_rel, int32_t stop_tet, bool slot_i3) {
     typedef typename RealOf<MODE>::T R;
     const float4 w0 = __ldcs(reinterpret_cast<const float4 *>(rp));
     const float4 w1 = __ldcs(reinterpret_cast<const float4 *>(rp) + 1);
@@ -311,7 +217,6 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
             }
         }
     }
-    bool ended = true;
     if (!ok)
         put_end(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_START);
     else if (T == stop_tet)  // the ray starts in the light's tet: nothing lies in between
@@ -320,19 +225,7 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
         put_end(hp, S.prev, next, steps, sc.flags);
     else if ((int32_t)next == stop_tet)
         put_end(hp, (int32_t)next, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
-    else
-        ended = false;
-    if constexpr (MODE != FP64) {
-        if (wq) {  // the 16-byte face-entry walk takes its start record
-            if (ended)
-                wq[0] = make_int4(-1, 0, 0, 0);
-            else
-                start_record_face16(mv, B, S, T, next, steps, sc.flags, rp, bounded, hp, wq);
-            return;
-        }
-    }
-    if (ended) return;
-    if (slot_i3) {
+    else if (slot_i3) {
         // the face-entry walk starts from the next tet's fourth vertex
         const int4 cv = __ldg(mv.cold + 2 * (int64_t)next);
         const int32_t i3 = cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2;
@@ -371,8 +264,7 @@ start_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ra
             const BatchDesc &D = descs[s.m];
             start_one<MODE>(D.mesh, D.rays + s.local, D.hits + s.local, P.tau_rel, -1, P.slot_i3 != 0);
         } else {
-            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, stop, P.slot_i3 != 0,
-                            P.wsr ? P.wsr + kWsrWords * r : nullptr, P.bounded != 0);
+            start_one<MODE>(mv0, rays0 + r, hits0 + r, P.tau_rel, stop, P.slot_i3 != 0);
         }
     }
 }
@@ -508,6 +400,37 @@ finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ r
     }
 }
 
+template <class R, bool BOUNDED> struct Depth {
+    __device__ __forceinline__ void init(const float4 &, const float4 &) {}
+    __device__ __forceinline__ void set(int, const float4 &) {}
+    __device__ __forceinline__ bool far(const float4 &) const { return false; }
+    __device__ __forceinline__ void put(int, bool) {}
+    __device__ __forceinline__ bool beyond() const { return false; }
+};
+template <class R> struct Depth<R, true> {
+    // whether each entry-face vertex lies beyond t_max along the ray (bit k
+    // for slot k): three bits instead of three depths keep the bounded walk's
+    // state small
+    R dx, dy, dz, dod, zmax;
+    uint32_t bits;
+    __device__ __forceinline__ void init(const float4 &w0, const float4 &w1) {
+        dx = w1.x; dy = w1.y; dz = w1.z;
+        dod = rfma(dz, R(w0.z), rfma(dy, R(w0.y), rmul(dx, R(w0.x))));
+        zmax = R(w1.w) * rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
+        bits = 0;
+    }
+    __device__ __forceinline__ R depth(const float4 &p) const {
+        return rfma(dz, R(p.z), rfma(dy, R(p.y), rmul(dx, R(p.x)))) - dod;
+    }
+    __device__ __forceinline__ bool far(const float4 &p) const { return depth(p) > zmax; }
+    __device__ __forceinline__ void put(int slot, bool b) {
+        bits = (bits & ~(1u << slot)) | ((uint32_t)b << slot);
+    }
+    __device__ __forceinline__ void set(int slot, const float4 &p) { put(slot, far(p)); }
+    // the entry face of the next tet lies entirely beyond t_max
+    __device__ __forceinline__ bool beyond() const { return bits == 7u; }
+};
+
 // One tet record in the walk's format, and the decode of the neighbour across
 // the exit vertex ie (Sec. 3 and Alg. 3, 5, 7).  i0..i2 are the entry face,
 // i3 the new vertex; prev is the tet the walk came from.
@@ -613,7 +536,6 @@ struct WalkParams {
     int refill;
     int batch_steps;
     const int32_t *stop_tet;  // point-light rays (bounded walks only): DEVICE light tet, else null
-    const int4 *wsr;          // walk start records (see kWsrWords), or null
 };
 
 // Guard mode: one step of a parked ray, with the double-precision re-test of
@@ -729,13 +651,6 @@ template <int MODE> struct PackedRanks {
 template <int FMT> struct GuardInLoop {
     static constexpr bool value = TM_GUARD_IN_LOOP && (FMT == TM_FORMAT_FACE || FMT == TM_FORMAT_FACE16);
 };
-// Which walks take their rays from walk start records (single-mesh launches
-// of the 16-byte face-entry walk in the float32 modes; a parked step would
-// need the hit-slot record, so guard mode only with the in-loop re-test).
-template <int MODE, int FMT, bool MULTI> struct UsesWsr {
-    static constexpr bool value = FMT == TM_FORMAT_FACE16 && MODE != FP64 && !MULTI &&
-                                  (MODE != FP32G || GuardInLoop<FMT>::value);
-};
 
 // Guard mode, 16-byte face entries: the walk keeps the ranks of its
 // vertices among the current tet's ids, so the re-test of one sign test
@@ -817,7 +732,6 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
     uint32_t steps = 0;
     const int32_t stop = (BOUNDED && !MULTI) ? load_stop(P.stop_tet, mv0.nt) : -1;
     bool far3 = false;  // face entries, bounded walks: the current tet's fourth vertex lies beyond t_max
-    int32_t ray_i = 0;  // the ray a refilled lane takes (single-mesh launches)
 
     for (;;) {
         bool load = false;
@@ -853,7 +767,6 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     sc.ray = rays0 + local;
                     hp = hits0 + local;
                 }
-                ray_i = local;
                 load = true;
             }
             if (BOUNDED && !MULTI) {
@@ -865,65 +778,12 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 // refill rarely, lose a little to the extra instructions.
                 const unsigned long long rq = base + kRefillPrefetchAhead + (unsigned long long)lane;
                 if (lane < n_idle && rq < (unsigned long long)n) {
-                    if (UsesWsr<MODE, FMT, MULTI>::value) {
-                        const int4 *q = P.wsr + kWsrWords * rq;
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(q + kWsrWords - 1));
-                    } else {
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(hits0 + rq));
-                    }
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(hits0 + rq));
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(rays0 + rq));
                 }
             }
         }
-        if (UsesWsr<MODE, FMT, MULTI>::value && load) {
-            // the walk start record: independent reads only (and the ray
-            // itself for the t_max test of bounded walks)
-            const int4 *q = P.wsr + kWsrWords * (int64_t)ray_i;
-            const int4 q0 = __ldcs(q), q1 = __ldcs(q + 1), q2 = __ldcs(q + 2), q3 = __ldcs(q + 3),
-                       q4 = __ldcs(q + 4);
-            float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
-            if (BOUNDED) {
-                w0 = __ldg(reinterpret_cast<const float4 *>(sc.ray));
-                w1 = __ldg(reinterpret_cast<const float4 *>(sc.ray) + 1);
-            }
-            if (q0.x >= 0) {  // else the ray ended in the start phase, which wrote its hit slot
-                S.tet = q0.x;
-                steps = (uint32_t)q0.z;
-                sc.flags = (uint32_t)q0.w;
-                B.ux = R(__int_as_float(q1.x)); B.uy = R(__int_as_float(q1.y));
-                B.uz = R(__int_as_float(q1.z)); B.pox = R(__int_as_float(q1.w));
-                B.vx = R(__int_as_float(q2.x)); B.vy = R(__int_as_float(q2.y));
-                B.vz = R(__int_as_float(q2.z)); B.poy = R(__int_as_float(q2.w));
-                S.p0.x = R(__int_as_float(q3.x)); S.p0.y = R(__int_as_float(q3.y));
-                S.p1.x = R(__int_as_float(q3.z)); S.p1.y = R(__int_as_float(q3.w));
-                S.p2.x = R(__int_as_float(q4.x)); S.p2.y = R(__int_as_float(q4.y));
-                S.p3.x = R(__int_as_float(q4.z)); S.p3.y = R(__int_as_float(q4.w));
-                if (MODE == FP32G) {
-                    S.m0 = guard_mag(S.p0, sc.tau);
-                    S.m1 = guard_mag(S.p1, sc.tau);
-                    S.m2 = guard_mag(S.p2, sc.tau);
-                    S.m3 = guard_mag(S.p3, sc.tau);
-                }
-                const uint32_t F = (uint32_t)q0.y;
-                if (BOUNDED) {
-                    Z.init(w0, w1);
-                    Z.put(0, (F >> 7) & 1u);
-                    Z.put(1, (F >> 15) & 1u);
-                    Z.put(2, (F >> 23) & 1u);
-                    far3 = (F >> 31) != 0;
-                }
-                if (PackedRanks<MODE>::value) {
-                    S.i0 = (int32_t)(F & kWsrRanks);
-                } else {
-                    S.i0 = (int32_t)(F & 3u);
-                    S.i1 = (int32_t)((F >> 8) & 3u);
-                    S.i2 = (int32_t)((F >> 16) & 3u);
-                    S.i3 = (int32_t)((F >> 24) & 3u);
-                }
-                active = true;
-            }
-        } else if (load) {
+        if (load) {
             // the walk record and the ray in one round trip
             const int4 a = __ldcg(reinterpret_cast<const int4 *>(hp));
             const int4 b = __ldcg(reinterpret_cast<const int4 *>(hp) + 1);
@@ -1266,8 +1126,6 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     P.tau_rel = W.tau_rel;
     P.stop_tet = MULTI ? nullptr : W.stop_tet;
     P.slot_i3 = FMT == TM_FORMAT_FACE || FMT == TM_FORMAT_FACE16;
-    P.wsr = UsesWsr<MODE, FMT, MULTI>::value ? const_cast<int4 *>(W.wsr) : nullptr;
-    P.bounded = BOUNDED;
     const int sms = sm_count_cached();
     int64_t g = (W.n_cap + 255) / 256;
     const int64_t gmax = (int64_t)sms * TM_PHASE_CTAS_PER_SM;
@@ -1340,7 +1198,7 @@ TraceConfig resolve_trace_opts(const tm_trace_opts *o, int64_t nt) {
     c.tau = (o && o->guard_tau > 0.f) ? o->guard_tau : 1e-6f;
     const double side = std::cbrt((double)(nt > 0 ? nt : 1));
     c.max_steps = (o && o->max_steps) ? o->max_steps : (uint32_t)(4.0 * side * 8.0 + 256.0);
-    c.refill = (o && o->refill) ? o->refill : 8;
+    c.refill = (o && o->refill) ? o->refill : 4;
     c.batch_steps = (o && o->batch_steps) ? o->batch_steps : 16;
     c.ctas_per_sm = o ? o->ctas_per_sm : 0;
     c.bounded = o ? o->tmax_early_exit != 0 : false;
@@ -1366,33 +1224,6 @@ int auto_format(bool has_faces16, bool has_faces) {
     return has_faces16 ? TM_FORMAT_FACE16 : (has_faces ? TM_FORMAT_FACE : TM_FORMAT_TET32);
 }
 
-// Host side of UsesWsr for a single-mesh launch.
-static bool uses_wsr(int mode, int format) {
-    switch (mode) {
-        case FP32G: return format == TM_FORMAT_FACE16 && UsesWsr<FP32G, TM_FORMAT_FACE16, false>::value;
-        case FP32: return format == TM_FORMAT_FACE16 && UsesWsr<FP32, TM_FORMAT_FACE16, false>::value;
-        default: return false;
-    }
-}
-
-// Stream-ordered scratch comes from the device's default memory pool.  By
-// default a pool returns its memory at every synchronisation, and the next
-// trace would map its scratch again; keep it instead (once per device).
-static void keep_pool_memory() {
-    static std::mutex mu;
-    static bool done[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-    std::lock_guard<std::mutex> lock(mu);
-    if (done[dev]) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t keep = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
-    done[dev] = true;
-}
-
 tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const int64_t *n_dev,
                        tm_hit *hits, const TraceConfig &cfg_in, cudaStream_t s) {
     TraceConfig cfg = cfg_in;
@@ -1401,12 +1232,8 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
     if (!valid_config(cfg)) return TM_ERR_ARG;
     if (n == 0) return TM_OK;
     if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
-    // scratch: the walk's ray counter, then the walk start records (80 B a ray)
-    const bool wsr = uses_wsr(cfg.mode, cfg.format);
-    const size_t bytes = 256 + (wsr ? sizeof(int4) * kWsrWords * (size_t)n : 0);
-    if (wsr) keep_pool_memory();
-    unsigned long long *cursor = nullptr;
-    TM_CUDA(cudaMallocAsync((void **)&cursor, bytes, s));
+    unsigned long long *cursor = nullptr;  // the walk's ray counter
+    TM_CUDA(cudaMallocAsync((void **)&cursor, sizeof(unsigned long long), s));
     const cudaError_t ez = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s);
     if (ez != cudaSuccess) {
         cudaFreeAsync(cursor, s);
@@ -1422,7 +1249,6 @@ tm_status launch_trace(const MeshView &mv, const tm_ray *rays, int64_t n, const 
     W.refill = cfg.refill;
     W.batch_steps = cfg.batch_steps;
     W.stop_tet = cfg.stop_tet;
-    W.wsr = wsr ? reinterpret_cast<const int4 *>(reinterpret_cast<char *>(cursor) + 256) : nullptr;
     int sms = 0;
     int per_sm = max_persistent_ctas(cfg.mode, false, cfg.bounded, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
@@ -1456,7 +1282,6 @@ tm_status launch_trace_batch(const BatchDesc *descs_dev, int n_meshes, int64_t t
     W.refill = cfg.refill;
     W.batch_steps = cfg.batch_steps;
     W.stop_tet = nullptr;
-    W.wsr = nullptr;
     int sms = 0;
     int per_sm = max_persistent_ctas(cfg.mode, true, false, cfg.block, &sms);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;

@@ -193,9 +193,6 @@ template <class R> struct WalkState {
     int32_t i3;
     P2<R> p3;
     float m3;
-    // line init: rank of the tet's vertex opposite the exit face among its
-    // four ids (the index of the exit face's 16-byte face entry)
-    int xr;
 };
 
 
@@ -228,7 +225,6 @@ __device__ __forceinline__ bool line_init_core(const Basis<R> &B, int32_t T, int
     }
     if (count != 1) return false;
     // counter-clockwise order of the exit face: reverse its inward order
-    int32_t vx = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (k == found) {
@@ -237,10 +233,8 @@ __device__ __forceinline__ bool line_init_core(const Basis<R> &B, int32_t T, int
             S.i1 = V[d]; S.p1 = P[d];
             S.i2 = V[b]; S.p2 = P[b];
             next = NB[k];
-            vx = V[k];
         }
     }
-    S.xr = (V[0] < vx) + (V[1] < vx) + (V[2] < vx) + (V[3] < vx);
     S.prev = T;
     S.m0 = guard_mag(S.p0, c.tau);
     S.m1 = guard_mag(S.p1, c.tau);

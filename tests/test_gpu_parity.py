@@ -211,6 +211,9 @@ def test_gen_secondary_matches_generator(tmx, tiny):
         k = int(cnt.item())
         r2 = r2[:k].cpu().numpy()
         src = src[:k].cpu().numpy()
+        # the generator groups the hits by length bucket: back to hit order
+        order = np.argsort(src, kind="stable")
+        r2, src = r2[order], src[order]
         o2, d2, tm2, entry, src_o = secondary_rays(tiny.s.points, tiny.s.tris, w["tri"],
                                                    np.float32(w["b1"]), np.float32(w["b2"]), side,
                                                    1234, per_hit, tmax)
@@ -220,6 +223,48 @@ def test_gen_secondary_matches_generator(tmx, tiny):
         assert np.abs(r2[:, 0:3] - o2).max() < 1e-6
         assert np.abs(r2[:, 4:7] - d2).max() < 2e-5
         assert np.array_equal(r2[:, 7], tm2)
+
+
+def host_length_bucket(lo, hi, extent, o, d, tmax, buckets=8):
+    """The generator's length bucket of rays (float32, as on the device):
+    the distance to the bounding box along d (or t_max) over the extent."""
+    f = np.float32
+    o = np.asarray(o, f); d = np.asarray(d, f)
+    t = np.full(len(o), f(tmax), f)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for a in range(3):
+            up = (f(hi[a]) - o[:, a]) / d[:, a]
+            dn = (f(lo[a]) - o[:, a]) / d[:, a]
+            t = np.where(d[:, a] > 0, np.minimum(t, up), np.where(d[:, a] < 0, np.minimum(t, dn), t))
+    ln = t / f(extent)
+    b = ((f(1) - np.maximum(ln, f(0))) * f(buckets)).astype(np.int64)
+    return np.where(ln < 1, np.minimum(b, buckets - 1), 0), ln
+
+
+def test_secondary_rays_grouped_by_length_bucket(tmx, precision):
+    """Diffuse bounce rays come out bucket by bucket, the longest possible
+    walks first, hits in order within a bucket; as a set they are the rays
+    of every hit."""
+    c = precision
+    cam = c.s.camera
+    start = dev(np.array([c.cam_internal], np.int32))
+    hits = c.mesh.trace(tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, cam.width, cam.height),
+                                        start))
+    r2, cnt, src = c.mesh.gen_secondary(hits, 1, np.inf, seed=5, src=True)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    r2, src = r2[:k].cpu().numpy(), src[:k].cpu().numpy()
+    hit = tmx.unpack_hits(hits)["tri"] >= 0
+    assert np.array_equal(np.sort(src), np.nonzero(hit)[0])      # every hit once
+    info = c.mesh.info
+    b, ln = host_length_bucket(info.bbox_lo, info.bbox_hi, info.extent, r2[:, 0:3], r2[:, 4:7],
+                               np.inf)
+    edge = np.abs(ln * 8 - np.round(ln * 8)) < 1e-5               # float ties at a bucket edge
+    ok = ~edge
+    assert (np.diff(b[ok]) >= 0).all()                          # farthest bucket first
+    for g in np.unique(b[ok]):                                  # hit order inside a bucket
+        assert (np.diff(src[ok][b[ok] == g]) > 0).all()
+    assert len(np.unique(b)) >= 4                               # the bounce rays do spread out
 
 
 @pytest.mark.parametrize("mode", ["fp32g", "fp32", "fp64"])
@@ -452,6 +497,52 @@ def test_batch_matches_single_launches(tmx, faces):
         if wnt is not None:
             assert np.array_equal(tmx.unpack_hits(h)["tri"], wnt["tri"])
     b.close()
+
+
+def test_step_captured_in_a_cuda_graph_equals_eager_calls(tmx):
+    """The bench replays its step (locate, primary rays, trace, bounce rays,
+    trace with the device count) from a CUDA graph captured from the API
+    calls; replays give exactly the hits of the eager calls, twice in a row."""
+    s = sg.make_config("medium", n_override=24)
+    mesh = tmx.Mesh(s.points, s.tets, s.tris, faces16=True)
+    cam = tmx.make_camera(s.camera.eye, s.camera.fov_deg, 320, 180)
+    n = 320 * 180
+    eye = torch.tensor([s.camera.eye], dtype=torch.float32, device="cuda")
+    start = torch.empty(1, dtype=torch.int32, device="cuda")
+    rays = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    hits = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    rays2 = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    hits2 = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def step():
+        mesh.locate(eye, out=start)
+        tmx.gen_primary(cam, start, rays=rays)
+        mesh.trace(rays, hits=hits)
+        mesh.gen_secondary(hits, 1, np.inf, seed=3, rays_out=rays2, count=count)
+        mesh.trace(rays2, hits=hits2, n_dev=count)
+    step()
+    torch.cuda.synchronize()
+    k = int(count.item())
+    # (a restart ray's start code is a negative int32 in a float slot: compare bits)
+    want = (hits.clone(), rays2[:k].view(torch.int32).clone(), hits2[:k].clone())
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(2):
+        for t in (hits, rays2, hits2):
+            t.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(count.item()) == k
+        assert torch.equal(hits, want[0])
+        assert torch.equal(rays2[:k].view(torch.int32), want[1]) and torch.equal(hits2[:k], want[2])
 
 
 def test_edge_cases(tmx, tiny):
