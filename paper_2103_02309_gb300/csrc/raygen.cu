@@ -76,62 +76,50 @@ count_hits_kernel(const tm_hit *__restrict__ hits, int64_t n, const int64_t *n_d
 }
 
 // Exclusive scan of the block counts in one block; total at offsets[nb].
-// Each thread sums a contiguous segment of the counts, the block scans the
-// segment sums, then each thread writes its segment's offsets: one pass for
-// any number of counts (the diffuse generator has one per block and length
-// bucket).
+// Each warp takes a contiguous segment of the counts and reads it 32 at a
+// time (one coalesced line per read): first the segment's sum, then, after
+// the block has scanned the 32 warp sums, the offsets, with a warp scan per
+// line and a running carry.  One pass for any number of counts (the diffuse
+// generator has one per block and length bucket).
 __global__ void __launch_bounds__(kScanBlock)
 scan_counts_kernel(const int32_t *__restrict__ counts, int64_t nb, int64_t *__restrict__ offsets,
                    int per_hit, int64_t *__restrict__ count_out) {
-    __shared__ int64_t warp_sum[32];
+    constexpr int kWarps = kScanBlock / 32;
+    __shared__ int64_t warp_base[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t seg = (nb + kScanBlock - 1) / kScanBlock;
-    const int64_t lo = min(nb, threadIdx.x * seg), hi = min(nb, lo + seg);
+    const int64_t seg = (nb + kWarps - 1) / kWarps;
+    const int64_t lo = min(nb, warp * seg), hi = min(nb, lo + seg);
     int64_t v = 0;
-    int64_t i = lo;
-    for (; i + 8 <= hi; i += 8) {  // eight independent loads in flight
-        int32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = __ldcg(counts + i + k);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v += c[k];
-    }
-    for (; i < hi; ++i) v += __ldcg(counts + i);
-    int64_t x = v;  // inclusive scan of the segment sums: warps, then across warps
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sum[warp] = x;
+#pragma unroll 4
+    for (int64_t i = lo + lane; i < hi; i += 32) v += __ldcg(counts + i);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) warp_base[warp] = v;
     __syncthreads();
-    if (warp == 0) {
-        int64_t w = warp_sum[lane];
+    if (warp == 0) {  // exclusive scan of the warp sums
+        const int64_t w = warp_base[lane];
+        int64_t x = w;
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        warp_sum[lane] = w;
+        warp_base[lane] = x - w;
+        if (lane == 31) {
+            offsets[nb] = x;
+            *count_out = x * per_hit;
+        }
     }
     __syncthreads();
-    int64_t acc = (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
-    i = lo;
-    for (; i + 8 <= hi; i += 8) {
-        int32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = __ldcg(counts + i + k);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            offsets[i + k] = acc;
-            acc += c[k];
+    int64_t carry = warp_base[warp];
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t i = base + lane;
+        const int64_t c = i < hi ? __ldcg(counts + i) : 0;
+        int64_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-    }
-    for (; i < hi; ++i) {
-        offsets[i] = acc;
-        acc += __ldcg(counts + i);
-    }
-    if (threadIdx.x == kScanBlock - 1) {
-        offsets[nb] = acc;
-        *count_out = acc * per_hit;
+        if (i < hi) offsets[i] = carry + x - c;
+        carry += __shfl_sync(0xffffffffu, x, 31);
     }
 }
 
@@ -314,7 +302,9 @@ __device__ __forceinline__ int64_t bucket_position(int b, const int64_t *offsets
     return offsets[(int64_t)b * gridDim.x + blockIdx.x] + before;
 }
 
-__global__ void __launch_bounds__(kScanBlock)
+// Two blocks an SM (32 registers): the pass waits on a hit, then on its
+// triangle, and more warps in flight hide more of that.
+__global__ void __launch_bounds__(kScanBlock, 2)
 emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
                       int64_t n, const int64_t *n_dev, const int64_t *__restrict__ offsets,
                       int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
