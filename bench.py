@@ -485,7 +485,7 @@ def run_ours(args, world, rank, local):
     frames = {"fp32g": capture()}
     phase_ms = {"primary": dict(zip(("start", "walk", "finish"), timed.phases[0])),
                 "secondary": dict(zip(("start", "walk", "finish"), timed.phases[1])),
-                "note": "event-timed per launch; start includes the ordering passes of the pool"}
+                "note": "event-timed per launch, eager steps (start: basis and first tet; finish: the hit)"}
     n_second = int(count.item())
     if tiles and world > 1:
         import torch.distributed as dist
