@@ -255,77 +255,115 @@ __device__ __forceinline__ int length_bucket(const MeshView &mv, float ox, float
     return b < kLengthBuckets ? b : kLengthBuckets - 1;
 }
 
-// Pass 1 of the diffuse / occlusion generator: counts[b * gridDim.x +
-// block] = hits of the block in length bucket b (a scan of the counts in
-// that order gives every bucket's blocks their place, bucket after bucket).
-__global__ void __launch_bounds__(kScanBlock)
+// The diffuse / occlusion generator's count pass runs kCountThreads threads
+// a block and its emit pass kEmitThreads; each thread takes PER = kScanBlock
+// / THREADS hits of the block's kScanBlock (hit base + j * THREADS + thread
+// for j = 0 .. PER-1, so every load is coalesced).  A thread issues the reads
+// of all its hits before it waits on any, and then the reads of their
+// triangles, instead of waiting on two dependent reads per hit.  Within a
+// block, hit order is (j, thread).  The emit pass holds more per hit, so it
+// takes fewer hits a thread and keeps more warps.
+constexpr int kCountThreads = 256;
+constexpr int kEmitThreads = 512;
+
+// Frames and buckets of this thread's hits (-1: no usable hit).
+template <int PER> struct GenHits {
+    HitIn h[PER];
+    BounceFrame f[PER];
+    float3 d0[PER];
+    int b[PER];
+};
+template <int THREADS, int PER>
+__device__ __forceinline__ void gen_hits(const MeshView &mv, const tm_hit *hits, int64_t n,
+                                         const int64_t *n_dev, int per_hit, float tmax,
+                                         uint64_t seed, GenHits<PER> &g) {
+    const int64_t nv = valid_count(n, n_dev);
+    const int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) g.h[j] = load_hit(hits, base + j * THREADS, nv, mv.nc);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        g.b[j] = -1;
+        if (g.h[j].hit) {
+            g.f[j] = bounce_frame(mv, g.h[j]);
+            g.d0[j] = bounce_dir(g.f[j], seed, base + j * THREADS, per_hit, 0);
+            g.b[j] = length_bucket(mv, g.f[j].ox, g.f[j].oy, g.f[j].oz, g.d0[j], tmax);
+        }
+    }
+}
+
+// Per warp and j, the hits of each bucket (ballots); every thread calls it.
+template <int THREADS, int PER>
+__device__ __forceinline__ void gen_ballots(const int (&b)[PER], int (*wc)[kLengthBuckets][THREADS / 32],
+                                            unsigned (&mine)[PER]) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        mine[j] = 0;
+#pragma unroll
+        for (int k = 0; k < kLengthBuckets; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, b[j] == k);
+            if (b[j] == k) mine[j] = m;
+            if (lane == 0) wc[j][k][warp] = __popc(m);
+        }
+    }
+}
+
+// Pass 1: counts[b * gridDim.x + block] = hits of the block in length
+// bucket b (a scan of the counts in that order gives every bucket's blocks
+// their place, bucket after bucket).
+__global__ void __launch_bounds__(kCountThreads)
 count_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
                        int64_t n, const int64_t *n_dev, int per_hit, float tmax, uint64_t seed,
                        int32_t *__restrict__ counts) {
-    __shared__ int bc[kLengthBuckets];
-    if (threadIdx.x < kLengthBuckets) bc[threadIdx.x] = 0;
+    constexpr int PER = kScanBlock / kCountThreads;
+    __shared__ int wc[PER][kLengthBuckets][kCountThreads / 32];
+    GenHits<PER> g;
+    gen_hits<kCountThreads, PER>(mv, hits, n, n_dev, per_hit, tmax, seed, g);
+    unsigned mine[PER];
+    gen_ballots<kCountThreads, PER>(g.b, wc, mine);
     __syncthreads();
-    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    const HitIn h = load_hit(hits, i, valid_count(n, n_dev), mv.nc);
-    int b = -1;
-    if (h.hit) {
-        const BounceFrame f = bounce_frame(mv, h);
-        b = length_bucket(mv, f.ox, f.oy, f.oz, bounce_dir(f, seed, i, per_hit, 0), tmax);
+    if (threadIdx.x < kLengthBuckets) {
+        int c = 0;
+        for (int j = 0; j < PER; ++j)
+            for (int w = 0; w < kCountThreads / 32; ++w) c += wc[j][threadIdx.x][w];
+        counts[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = c;
     }
-    const unsigned lane = threadIdx.x & 31u;
-#pragma unroll
-    for (int k = 0; k < kLengthBuckets; ++k) {
-        const unsigned m = __ballot_sync(0xffffffffu, b == k);
-        if (lane == 0 && m) atomicAdd(&bc[k], __popc(m));
-    }
-    __syncthreads();
-    if (threadIdx.x < kLengthBuckets) counts[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = bc[threadIdx.x];
 }
 
-// Output position (in hits) of this thread's hit in bucket b (-1: none):
-// its block's offset in that bucket plus the block's earlier hits of the
-// bucket.  Every thread of the block calls it.
-__device__ __forceinline__ int64_t bucket_position(int b, const int64_t *offsets) {
-    __shared__ int wc[kLengthBuckets][kScanBlock / 32];
-    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    unsigned mine = 0;
-#pragma unroll
-    for (int k = 0; k < kLengthBuckets; ++k) {
-        const unsigned m = __ballot_sync(0xffffffffu, b == k);
-        if (b == k) mine = m;
-        if (lane == 0) wc[k][warp] = __popc(m);
-    }
-    __syncthreads();
-    if (b < 0) return -1;
-    int before = __popc(mine & ((1u << lane) - 1u));
-    for (unsigned w = 0; w < warp; ++w) before += wc[b][w];
-    return offsets[(int64_t)b * gridDim.x + blockIdx.x] + before;
-}
-
-// Two blocks an SM (32 registers): the pass waits on a hit, then on its
-// triangle, and more warps in flight hide more of that.
-__global__ void __launch_bounds__(kScanBlock, 2)
+__global__ void __launch_bounds__(kEmitThreads, 2)
 emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
                       int64_t n, const int64_t *n_dev, const int64_t *__restrict__ offsets,
                       int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
                       int32_t *__restrict__ src) {
-    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
-    const HitIn h = load_hit(hits, i, valid_count(n, n_dev), mv.nc);
-    BounceFrame f;
-    float3 d0 = make_float3(0.f, 0.f, 0.f);
-    int b = -1;
-    if (h.hit) {
-        f = bounce_frame(mv, h);
-        d0 = bounce_dir(f, seed, i, per_hit, 0);
-        b = length_bucket(mv, f.ox, f.oy, f.oz, d0, tmax);
-    }
-    const int64_t pos = bucket_position(b, offsets);
-    if (b < 0) return;
-    for (int k = 0; k < per_hit; ++k) {
-        const float3 d = k == 0 ? d0 : bounce_dir(f, seed, i, per_hit, k);
-        const int64_t o = pos * per_hit + k;
-        put_ray(out, o, f.ox, f.oy, f.oz, f.start, d.x, d.y, d.z, tmax);
-        if (src) src[o] = (int32_t)i;
+    constexpr int PER = kScanBlock / kEmitThreads;
+    __shared__ int wc[PER][kLengthBuckets][kEmitThreads / 32];
+    GenHits<PER> g;
+    gen_hits<kEmitThreads, PER>(mv, hits, n, n_dev, per_hit, tmax, seed, g);
+    unsigned mine[PER];
+    gen_ballots<kEmitThreads, PER>(g.b, wc, mine);
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int b = g.b[j];
+        if (b < 0) continue;
+        // the block's earlier hits of bucket b: all warps of earlier j, then
+        // the earlier warps of this j, then the earlier lanes of this warp
+        int before = __popc(mine[j] & ((1u << lane) - 1u));
+        for (int jj = 0; jj < j; ++jj)
+            for (int w = 0; w < kEmitThreads / 32; ++w) before += wc[jj][b][w];
+        for (unsigned w = 0; w < warp; ++w) before += wc[j][b][w];
+        const int64_t pos = offsets[(int64_t)b * gridDim.x + blockIdx.x] + before;
+        const int64_t i = base + j * kEmitThreads;
+        const BounceFrame &f = g.f[j];
+        for (int k = 0; k < per_hit; ++k) {
+            const float3 d = k == 0 ? g.d0[j] : bounce_dir(f, seed, i, per_hit, k);
+            const int64_t o = pos * per_hit + k;
+            put_ray(out, o, f.ox, f.oy, f.oz, f.start, d.x, d.y, d.z, tmax);
+            if (src) src[o] = (int32_t)i;
+        }
     }
 }
 
@@ -483,10 +521,10 @@ tm_status launch_gen_secondary(const MeshView &mv, const tm_hit *hits, int64_t n
                                tm_ray *out, int64_t *count, int32_t *src, cudaStream_t s) {
     return gen_from_hits(hits, n, n_dev, mv.nc, per_hit, count, s, "gen_secondary launch",
                          [&](int nb, const int64_t *offsets) {
-                             tmk::emit_secondary_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
+                             tmk::emit_secondary_kernel<<<nb, tmk::kEmitThreads, 0, s>>>(
                                  mv, hits, n, n_dev, offsets, per_hit, tmax, seed, out, src);
                          }, tmk::kLengthBuckets, [&](int nb, int32_t *counts) {
-                             tmk::count_secondary_kernel<<<nb, tmk::kScanBlock, 0, s>>>(
+                             tmk::count_secondary_kernel<<<nb, tmk::kCountThreads, 0, s>>>(
                                  mv, hits, n, n_dev, per_hit, tmax, seed, counts);
                          });
 }
@@ -565,11 +603,11 @@ tm_status launch_gen_secondary_noalloc(const MeshView &mv, const tm_hit *hits, i
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     int32_t *counts = static_cast<int32_t *>(base);
     int64_t *offsets = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(base) + kNoallocCountBytes);
-    tmk::count_secondary_kernel<<<(int)nb, kScanBlock, 0, s>>>(mv, hits, n, n_dev, per_hit, tmax, seed,
+    tmk::count_secondary_kernel<<<(int)nb, tmk::kCountThreads, 0, s>>>(mv, hits, n, n_dev, per_hit, tmax, seed,
                                                                counts);
     tmk::scan_counts_kernel<<<1, kScanBlock, 0, s>>>(counts, nb * tmk::kLengthBuckets, offsets, per_hit,
                                                      count);
-    tmk::emit_secondary_kernel<<<(int)nb, kScanBlock, 0, s>>>(mv, hits, n, n_dev, offsets, per_hit,
+    tmk::emit_secondary_kernel<<<(int)nb, tmk::kEmitThreads, 0, s>>>(mv, hits, n, n_dev, offsets, per_hit,
                                                              tmax, seed, out, src);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

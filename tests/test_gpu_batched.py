@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-SAMPLES_PER_MESH = 150
+SAMPLES_PER_MESH = 2000
 
 
 @pytest.fixture(scope="module")
