@@ -612,6 +612,7 @@ def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world, f
     the step before and after it.  The timed region spans all steps, and every
     step copies its whole input in and all its hits out.
     """
+    from paper_2103_02309_gb300.shard import shard_seed
     start = mesh.locate(torch.tensor([s.camera.eye], dtype=torch.float32, device=dev))
     rays_dev = tmx.gen_primary(cam, start)
     rays_host = torch.empty_like(rays_dev, device="cpu").pin_memory()
@@ -650,7 +651,8 @@ def run_e2e(args, mesh, tmx, torch, s, cam, n_primary, per_hit, W, dev, world, f
             st.wait_event(ch["out_done"])       # the previous step's hits of the slice are home
             mesh.trace(ch["rays"], hits=ch["hits"], opts=o, stream=st)
             ch["prim_done"].record(st)
-            mesh.gen_secondary(ch["hits"], per_hit, W["tmax"], seed=0x5EED + c,
+            # the slice's rays draw the whole frame's random numbers
+            mesh.gen_secondary(ch["hits"], per_hit, W["tmax"], seed=shard_seed(0x5EED, ch["lo"], per_hit),
                                rays_out=ch["rays2"], count=ch["count"], stream=st)
             mesh.trace(ch["rays2"], hits=ch["hits2"], n_dev=ch["count"], opts=o2, stream=st)
             ch["comp_done"].record(st)

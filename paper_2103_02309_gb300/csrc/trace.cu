@@ -860,7 +860,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                 if constexpr (MODE == FP32G) {
                 // Alg. 1 reads two sign tests: det(p3, p0), then det(p3, p1) when it
                 // is positive, det(p3, p2) otherwise; only those two are guarded
-                const R d0 = det2(S.p3, S.p0);
+                const R d0 = det2_packed(S.p3, S.p0);
                 bool s0 = d0 > R(0);
                 if (MODE == FP32G) {
                     if (!(fabsf((float)d0) > fmaxf(S.m3, S.m0))) {
@@ -871,7 +871,7 @@ walk_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ ray
                     }
                 }
                 const P2<R> pk = s0 ? S.p1 : S.p2;
-                const R dk = det2(S.p3, pk);
+                const R dk = det2_packed(S.p3, pk);
                 bool sk = dk > R(0);
                 if (MODE == FP32G) {
                     if (!(fabsf((float)dk) > fmaxf(S.m3, s0 ? S.m1 : S.m2))) {

@@ -64,6 +64,27 @@ template <class R> __device__ __forceinline__ R det2(const P2<R> &a, const P2<R>
     return rsub(rmul(a.x, b.y), rmul(a.y, b.x));
 }
 
+// det2 for float with both products in one packed two-wide multiply
+// (mul.rn.f32x2, sm_100 and later): (a.y * b.x, a.x * b.y), then the
+// difference of the halves.  Each product and the difference are rounded
+// as in det2, so the result is the same bit for bit.
+#ifndef TM_PACKED_DET
+#define TM_PACKED_DET 1
+#endif
+__device__ __forceinline__ float det2_packed(const P2<float> &a, const P2<float> &b) {
+#if TM_PACKED_DET
+    unsigned long long A, B, Q;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.y), "f"(a.x));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b.x), "f"(b.y));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(Q) : "l"(A), "l"(B));
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(Q));
+    return __fsub_rn(hi, lo);
+#else
+    return det2(a, b);
+#endif
+}
+
 template <class R> struct Basis {
     R ux, uy, uz, vx, vy, vz, pox, poy;
 
