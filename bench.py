@@ -253,6 +253,13 @@ def walk_roofline(tet_steps, rays, walk_ms, trace_ms, step_ms, hbm, hbm_src, l2_
             "dram_frac": round(traffic / walk_s_launch / 1e9 / hbm, 4) if traffic else None,
             "l2_bytes": l2b,
             "l2_frac": round(l2b / walk_s_launch / 1e9 / l2_peak, 4) if l2b else None,
+            # what the hardware moved against the method's bytes (per launch)
+            "dram_over_algorithmic": round(traffic / (alg / 2), 4) if traffic else None,
+            "l2_over_algorithmic": round(l2b / (alg / 2), 4) if l2b else None,
+            # the paper's count of about 13 FP32 operations per tet step,
+            # over the walk time: reported, not the bound
+            "flops_per_tet_step": 13,
+            "tflops": round(tet_steps * 13 / (walk_ms * 1e-3) / 1e12, 2),
             "l2_read_peak_gbs": round(l2_peak, 1),
             "l2_peak_source": "measured here: a read probe (L1-bypassing 16-byte loads) over a "
                               "48 MiB buffer resident in L2",

@@ -55,6 +55,9 @@ def test_walk_roofline_counts_the_methods_bytes():
     assert r["frac_trace"] == round((32e9 + 188 * rays) / 5e-3 / 1e9 / 8000.0, 4)
     assert r["dram_frac"] == 0.0625                                # 1 GB per 2 ms launch
     assert r["l2_frac"] == round(4e9 / 2e-3 / 1e9 / 6000.0, 4)
+    assert r["dram_over_algorithmic"] == round(1e9 / 16e9, 4)       # 16 GB a launch
+    assert r["l2_over_algorithmic"] == 0.25
+    assert r["tflops"] == round(13e9 / 4e-3 / 1e12, 2)
     none = bench.walk_roofline(steps, rays, 4.0, 5.0, 6.0, 8000.0, "measured", 6000.0, 16, None,
                                "bounce")
     assert none["traffic"] is None and none["dram_frac"] is None and none["l2_frac"] is None
