@@ -537,7 +537,10 @@ def run_ours(args, world, rank, local):
                 a1, a2 = tmx.unpack_hits(hits), tmx.unpack_hits(hits2[:k])
                 st = int(a1["steps"].astype(np.int64).sum() + a2["steps"].astype(np.int64).sum())
                 arms[name]["roofline"] = walk_roofline(st, n_primary + k, awk, atr, ams, hbm, hbm_src,
-                                                       l2_peak, RECORD_BYTES["tet16"] + 16, None,
+                                                       l2_peak, RECORD_BYTES["tet16"] + 16,
+                                                       profiled_counters(
+                                                           f"{args.workload}_tet16",
+                                                           "" if default_run else "variant"),
                                                        kind)
         arms["fp32g_speedup_vs_fp64"] = round(value / arms["fp64"]["value"], 2)
         hits.copy_(keep[0]); hits2.copy_(keep[1]); rays2.copy_(keep[2]); count.copy_(keep[3])

@@ -140,3 +140,14 @@ def test_oracle_leg_compares_every_ray_of_every_arm():
     b = vs["fp64"]
     assert not b["meets_bar"] and b["secondary"]["unexcused"] == 1 and b["primary"]["mismatches"] == 0
     assert "every ray" in vs["sample"]
+
+
+def test_committed_walk_profiles_are_of_the_current_kernels():
+    """The ncu summaries that the bench's rooflines quote (the default walk
+    and the Tet16 arm's walk on the precision workload) were taken from the
+    kernel source as it stands; a change to the kernels leaves them stale
+    and the bench then reports their traffic as null."""
+    for name in ("precision", "precision_tet16"):
+        got = bench.profiled_counters(name)
+        assert got is not None, name
+        assert got["traffic_bytes_per_launch"] > 0 and got["l2_bytes_per_launch"] > 0
