@@ -90,7 +90,7 @@ scan_counts_kernel(const int32_t *__restrict__ counts, int64_t nb, int64_t *__re
     const int64_t seg = (nb + kWarps - 1) / kWarps;
     const int64_t lo = min(nb, warp * seg), hi = min(nb, lo + seg);
     int64_t v = 0;
-#pragma unroll 4
+#pragma unroll 8
     for (int64_t i = lo + lane; i < hi; i += 32) v += __ldcg(counts + i);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) warp_base[warp] = v;
@@ -109,17 +109,29 @@ scan_counts_kernel(const int32_t *__restrict__ counts, int64_t nb, int64_t *__re
         }
     }
     __syncthreads();
+    // kLines lines of counts are read before the first is scanned, so the
+    // reads' latency is paid once per kLines lines, not once per line; a
+    // line's sum (32 block counts of at most kScanBlock) fits in 32 bits
+    constexpr int kLines = 8;
     int64_t carry = warp_base[warp];
-    for (int64_t base = lo; base < hi; base += 32) {
-        const int64_t i = base + lane;
-        const int64_t c = i < hi ? __ldcg(counts + i) : 0;
-        int64_t x = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+    for (int64_t base = lo; base < hi; base += 32 * kLines) {
+        int c[kLines];
+#pragma unroll
+        for (int u = 0; u < kLines; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            c[u] = i < hi ? __ldcg(counts + i) : 0;
         }
-        if (i < hi) offsets[i] = carry + x - c;
-        carry += __shfl_sync(0xffffffffu, x, 31);
+#pragma unroll
+        for (int u = 0; u < kLines; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            int x = c[u];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (i < hi) offsets[i] = carry + (x - c[u]);
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
     }
 }
 
@@ -214,14 +226,26 @@ __device__ __forceinline__ BounceFrame bounce_frame(const MeshView &mv, const Hi
     f.start = -1 - (2 * c + side);
     return f;
 }
+// The hardware's approximate square root (relative error near 2^-23;
+// +0 at +0).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 // Direction k of hit i: draws 2 (i per_hit + k) and 2 (i per_hit + k) + 1.
 __device__ __forceinline__ float3 bounce_dir(const BounceFrame &f, uint64_t seed, int64_t i, int per_hit,
                                              int k) {
     const uint64_t cnt = 2ull * ((uint64_t)i * (uint64_t)per_hit + (uint64_t)k);
     const float u0 = uniform24(seed, cnt), u1 = uniform24(seed, cnt + 1);
+    // phi = 2 pi u0 = psi + pi with psi = 2 pi (u0 - 1/2) in [-pi, pi), the
+    // range of the fast sine and cosine (absolute error about 5e-7 there):
+    // sin phi = -sin psi, cos phi = -cos psi
     float sp, cp;
-    sincospif(2.f * u0, &sp, &cp);
-    const float s = sqrtf(u1), lz = sqrtf(fmaxf(0.f, 1.f - u1));
+    __sincosf(6.283185307f * (u0 - 0.5f), &sp, &cp);
+    sp = -sp;
+    cp = -cp;
+    const float s = sqrt_approx(u1), lz = sqrt_approx(fmaxf(0.f, 1.f - u1));
     float dx = s * cp * f.t1x + s * sp * f.t2x + lz * f.nx;
     float dy = s * cp * f.t1y + s * sp * f.t2y + lz * f.ny;
     float dz = s * cp * f.t1z + s * sp * f.t2z + lz * f.nz;
@@ -246,8 +270,9 @@ __device__ __forceinline__ int length_bucket(const MeshView &mv, float ox, float
     const float ov[3] = {ox, oy, oz}, dv[3] = {d.x, d.y, d.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (dv[a] > 0.f) t = fminf(t, (mv.hi[a] - ov[a]) / dv[a]);
-        else if (dv[a] < 0.f) t = fminf(t, (mv.lo[a] - ov[a]) / dv[a]);
+        // the bucket only orders the rays: a fast quotient (2 ulp) will do
+        if (dv[a] > 0.f) t = fminf(t, __fdividef(mv.hi[a] - ov[a], dv[a]));
+        else if (dv[a] < 0.f) t = fminf(t, __fdividef(mv.lo[a] - ov[a], dv[a]));
     }
     const float len = t / fmaxf(mv.extent, 1e-30f);   // d has unit length
     if (!(len < 1.f)) return 0;                        // also NaN
@@ -344,17 +369,30 @@ emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restr
     gen_ballots<kEmitThreads, PER>(g.b, wc, mine);
     __syncthreads();
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    // The block's hits of bucket b before (j, warp), in its hit order (j
+    // first, then warp): warp b scans bucket b's PER x warps counts, one a
+    // lane, and leaves the exclusive prefix in place.
+    constexpr int kWarps = kEmitThreads / 32;
+    static_assert(PER * kWarps == 32, "one count a lane");
+    if (warp < (unsigned)kLengthBuckets) {
+        int *cell = &wc[lane / kWarps][warp][lane % kWarps];
+        const int v = *cell;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        *cell = x - v;
+    }
+    __syncthreads();
     const int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int b = g.b[j];
         if (b < 0) continue;
-        // the block's earlier hits of bucket b: all warps of earlier j, then
-        // the earlier warps of this j, then the earlier lanes of this warp
-        int before = __popc(mine[j] & ((1u << lane) - 1u));
-        for (int jj = 0; jj < j; ++jj)
-            for (int w = 0; w < kEmitThreads / 32; ++w) before += wc[jj][b][w];
-        for (unsigned w = 0; w < warp; ++w) before += wc[j][b][w];
+        // the block's earlier hits of bucket b: those before (j, warp), then
+        // the earlier lanes of this warp
+        const int before = wc[j][b][warp] + __popc(mine[j] & ((1u << lane) - 1u));
         const int64_t pos = offsets[(int64_t)b * gridDim.x + blockIdx.x] + before;
         const int64_t i = base + j * kEmitThreads;
         const BounceFrame &f = g.f[j];

@@ -232,13 +232,21 @@ __device__ __forceinline__ bool line_init_core(const Basis<R> &B, int32_t T, int
     P2<R> P[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) P[k] = B.project(X[k][0], X[k][1], X[k][2]);
+    // The six edges' orientations, each decided once; a face that runs an
+    // edge the other way reads the negation, so the four faces agree on
+    // every edge whatever the rounding of the re-test.
+    bool s[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j) s[i][j] = pos<MODE>(P[i], P[j], V[i], V[j], c);
+    auto ccw = [&](int i, int j) { return i < j ? s[i][j] : !s[j][i]; };
     int found = -1, count = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (k == skip) continue;
         const int a = face_in(k, 0), b = face_in(k, 1), d = face_in(k, 2);
-        const bool cw = !pos<MODE>(P[a], P[b], V[a], V[b], c) && !pos<MODE>(P[b], P[d], V[b], V[d], c) &&
-                        !pos<MODE>(P[d], P[a], V[d], V[a], c);
+        const bool cw = !ccw(a, b) && !ccw(b, d) && !ccw(d, a);
         if (cw) {
             if (found < 0) found = k;
             ++count;
