@@ -362,6 +362,15 @@ constexpr int kFinishBlock = 256;
 #define TM_FINISH_RAYS_PER_THREAD 4
 #endif
 constexpr int kFinishChunk = kFinishBlock * TM_FINISH_RAYS_PER_THREAD;
+// At the start of a chunk each thread pulls into L2 the end records (1), or
+// the end records and the rays (2), of its later rays, so that their reads
+// do not each wait on DRAM in turn.  Measured on GB300 (2): the finish
+// phases 8 % faster on the precision workload and on the large scene's
+// occlusion rays, though most of those end without a hit and never read
+// their ray; (1) gained half of that.
+#ifndef TM_FINISH_PREFETCH
+#define TM_FINISH_PREFETCH 2
+#endif
 
 // In guard mode about one hit in twenty needs the double-precision test,
 // and on GB300's narrow FP64 pipe a warp pays for it if any of its lanes
@@ -382,6 +391,15 @@ finish_kernel(const __grid_constant__ MeshView mv0, const tm_ray *__restrict__ r
         for (int64_t base = blockIdx.x * (int64_t)kFinishChunk; base < n;
              base += (int64_t)gridDim.x * kFinishChunk) {
             if (threadIdx.x == 0) queued = 0;
+            if (TM_FINISH_PREFETCH && !MULTI) {
+                for (int j = threadIdx.x + kFinishBlock; j < kFinishChunk; j += kFinishBlock) {
+                    const int64_t r = base + j;
+                    if (r < n) {
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(hits0 + r));
+                        if (TM_FINISH_PREFETCH > 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(rays0 + r));
+                    }
+                }
+            }
             __syncthreads();
             for (int j = threadIdx.x; j < kFinishChunk; j += kFinishBlock) {
                 const int64_t r = base + j;
