@@ -141,7 +141,9 @@ typedef struct {
 #define TM_HIT_SIDE_NEG   0x01u  /* the ray arrived from the - side of the hit triangle */
 #define TM_HIT_STEP_LIMIT 0x02u  /* max_steps reached; reported as a miss */
 #define TM_HIT_GUARD      0x04u  /* at least one sign test was re-decided in FP64 */
-#define TM_HIT_BAD_START  0x08u  /* origin not in the start tet, or an invalid restart face */
+#define TM_HIT_BAD_START  0x08u  /* origin not in the start tet, an invalid restart face, or a
+                                     ray without a line (d zero or not finite, o not finite);
+                                     such a ray is a miss with tet -1 and steps 0 */
 #define TM_HIT_TIE        0x10u  /* an exactly zero sign test was broken by vertex ids */
 #define TM_HIT_FINAL_FP64 0x20u  /* t and barycentrics recomputed in FP64 */
 #define TM_HIT_RESTART_3D 0x40u  /* a restart used the 3-D face-plane fallback step */

@@ -178,7 +178,12 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
     uint32_t next = TM_BOUNDARY;
     int32_t T = -1;
     bool ok = false;
-    if (start >= 0) {
+    // a ray without a line (a zero or non-finite direction, or a non-finite
+    // origin) has no walk: it ends here as a flagged miss
+    const bool line = isfinite(w0.x) && isfinite(w0.y) && isfinite(w0.z) && isfinite(w1.x) &&
+                      isfinite(w1.y) && isfinite(w1.z) && (w1.x != 0.f || w1.y != 0.f || w1.z != 0.f);
+    if (!line) {
+    } else if (start >= 0) {
         if (start < mv.nt) {
             T = start;
             ok = line_init<MODE>(mv, B, T, -1, sc, S, next);

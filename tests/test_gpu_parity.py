@@ -560,6 +560,24 @@ def test_edge_cases(tmx, tiny):
     far = tmx.pack_rays(np.array([[0.9, 0.9, 0.9]], np.float32), d[:1], np.inf, tiny.cam_internal)
     g = tmx.unpack_hits(m.trace(dev(far)))
     assert g["flags"][0] & tmx.HIT_BAD_START
+    # a ray without a line (zero or non-finite direction, non-finite origin)
+    # ends at once as a flagged miss, bounded walk or not
+    o3 = np.array([[0.5, 0.5, 0.05]] * 5, np.float32)
+    o3[3, 0], o3[4, 1] = np.nan, np.inf
+    d3 = np.array([[0, 0, 0], [np.nan, 0, 1], [0, np.inf, 1], [0, 0, 1], [0, 0, 1]], np.float32)
+    for early in (False, True):
+        g = tmx.unpack_hits(m.trace(dev(tmx.pack_rays(o3, d3, np.inf, tiny.cam_internal)),
+                                    tmax_early_exit=early))
+        assert (g["tri"] == -1).all() and (g["flags"] & tmx.HIT_BAD_START).all()
+        assert (g["steps"] == 0).all() and (g["tet"] == -1).all()
+    # t_max of zero or below: no hit, bounded walk or not
+    oc, dc = sg.camera_rays(tiny.s.camera)
+    for tmax in (0.0, -1.0):
+        for early in (False, True):
+            g = tmx.unpack_hits(m.trace(dev(tmx.pack_rays(oc, dc, tmax, tiny.cam_internal)),
+                                        tmax_early_exit=early))
+            assert (g["tri"] == -1).all()
+            assert (g["flags"] & (tmx.HIT_BAD_START | tmx.HIT_BAD_ID) == 0).all()
     # the step bound ends a walk as a flagged miss
     o2, d2 = sg.camera_rays(tiny.s.camera)
     g = tmx.unpack_hits(m.trace(dev(tmx.pack_rays(o2, d2, np.inf, tiny.cam_internal)), max_steps=2))
