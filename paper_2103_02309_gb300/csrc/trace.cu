@@ -242,14 +242,16 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
 
 // The start phase chases three or four dependent reads per ray (the ray,
 // its restart face, the tet's record and points, the next tet's record) and
-// is latency-bound: capped at 64 registers it runs four blocks of 256 an SM
-// instead of two, with some spill on its rare paths, and measured 20 %
-// faster on bounce and ambient-occlusion rays.  (The double-precision arm,
-// whose state is twice as wide, keeps its registers.)  The finish phase
-// keeps four blocks an SM at 64 registers as well, which it fits without
-// spilling.
+// is latency-bound, so it wants warps in flight, but it also holds much
+// state.  Measured on GB300 (start of camera / bounce / occlusion rays):
+// three blocks of 256 an SM at 80 registers (72 bytes of spill) 12-18 %
+// faster than four at 64 (368 bytes of spill: a ray's spills went to L2,
+// three sectors each way) and than two at 104 (no spill, 16 warps).  (The
+// double-precision arm, whose state is twice as wide, keeps its
+// registers.)  The finish phase keeps four blocks an SM at 64 registers,
+// which it fits without spilling.
 #ifndef TM_START_MIN_BLOCKS
-#define TM_START_MIN_BLOCKS 4
+#define TM_START_MIN_BLOCKS 3
 #endif
 #ifndef TM_FINISH_MIN_BLOCKS
 #define TM_FINISH_MIN_BLOCKS 4
