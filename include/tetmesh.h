@@ -109,6 +109,11 @@ enum {
     TM_FORMAT_FACE16 = 6
 };
 
+/* Ray and hit buffers (every tm_ray and tm_hit array passed to this
+ * library) must be 32-byte aligned, as each record is 32 bytes and is read
+ * and written whole; calls refuse other pointers with TM_ERR_ARG before any
+ * launch. */
+
 /* A ray, 32 bytes, two 16-byte words.
  *   start >= 0 : internal id of a tet that holds the origin (o).
  *   start <  0 : restart from a constrained face (Sec. 6): with
@@ -280,7 +285,7 @@ tm_status tm_locate(const tm_mesh *mesh, const float *q, int64_t n, const int32_
  * between them.  If n_dev is not
  * NULL it points to a DEVICE int64 holding the ray count (read by the
  * kernel, clamped to n), so that counts produced on the device need no host
- * round trip.  opts may be NULL (defaults).  rays and hits must be 16-byte
+ * round trip.  opts may be NULL (defaults).  rays and hits must be 32-byte
  * aligned.  Errors: TM_ERR_ARG, TM_ERR_NO_DEVICE, TM_ERR_CUDA, and
  * TM_ERR_TOO_LARGE for n > 2^31 - 1 (refused before any buffer is read). */
 tm_status tm_trace(const tm_mesh *mesh, const tm_ray *rays, int64_t n, const int64_t *n_dev,

@@ -162,7 +162,7 @@ tm_status tm_batch_set(tm_batch *b, const tm_ray *const *rays, const int64_t *n,
     std::vector<int4> chunks;
     for (int i = 0; i < nm; ++i) {
         if (n[i] < 0 || (n[i] > 0 && (!rays[i] || !hits[i]))) return TM_ERR_ARG;
-        if ((((uintptr_t)rays[i]) | ((uintptr_t)hits[i])) & 15u) return TM_ERR_ARG;
+        if ((((uintptr_t)rays[i]) | ((uintptr_t)hits[i])) & 31u) return TM_ERR_ARG;
         if (n[i] > INT32_MAX) return TM_ERR_TOO_LARGE;
         max_nt = std::max<int64_t>(max_nt, b->meshes[(size_t)i]->nt);
         BatchDesc &D = b->descs[(size_t)i];

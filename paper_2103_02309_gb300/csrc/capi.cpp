@@ -179,7 +179,7 @@ tm_status tm_locate(const tm_mesh *m, const float *q, int64_t n, const int32_t *
 tm_status tm_trace(const tm_mesh *m, const tm_ray *rays, int64_t n, const int64_t *n_dev,
                    tm_hit *hits, const tm_trace_opts *opts, void *stream) {
     if (!m || n < 0 || (n > 0 && (!rays || !hits))) return TM_ERR_ARG;
-    if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 31u) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     const TraceConfig cfg = resolve_trace_opts(opts, m->nt);
     if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
@@ -193,7 +193,7 @@ tm_status tm_trace_shadow(const tm_mesh *m, const tm_ray *rays, int64_t n, const
                           const int32_t *light_tet_dev, tm_hit *hits, const tm_trace_opts *opts,
                           void *stream) {
     if (!m || n < 0 || !light_tet_dev || (n > 0 && (!rays || !hits))) return TM_ERR_ARG;
-    if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if ((((uintptr_t)rays) | ((uintptr_t)hits)) & 31u) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     TraceConfig cfg = resolve_trace_opts(opts, m->nt);
     if (cfg.format == TM_FORMAT_TET20 && !m->d_t20) return TM_ERR_ARG;
@@ -208,7 +208,7 @@ tm_status tm_trace_shadow(const tm_mesh *m, const tm_ray *rays, int64_t n, const
 tm_status tm_gen_primary(const tm_camera *cam, const int32_t *start_dev, float tmax, tm_ray *rays,
                          void *stream) {
     if (!cam || !start_dev || !rays || cam->width < 0 || cam->height < 0) return TM_ERR_ARG;
-    if (((uintptr_t)rays) & 15u) return TM_ERR_ARG;
+    if (((uintptr_t)rays) & 31u) return TM_ERR_ARG;
     return launch_gen_primary(cam, start_dev, tmax, rays, (cudaStream_t)stream);
 }
 
@@ -217,7 +217,7 @@ tm_status tm_gen_secondary(const tm_mesh *m, const tm_hit *hits, int64_t n, cons
                            int64_t *count_dev, int32_t *src_out, void *stream) {
     if (!m || n < 0 || per_hit < 1 || per_hit > 1024 || !count_dev || (n > 0 && (!hits || !rays_out)))
         return TM_ERR_ARG;
-    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 31u) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     if (n * (int64_t)per_hit > INT32_MAX) return TM_ERR_TOO_LARGE;
     return launch_gen_secondary(mesh_view(m), hits, n, n_dev, per_hit, tmax, seed, rays_out, count_dev,
@@ -228,7 +228,7 @@ tm_status tm_gen_shadow(const tm_mesh *m, const tm_hit *hits, int64_t n, const i
                         float lx, float ly, float lz, tm_ray *rays_out, int64_t *count_dev,
                         int32_t *src_out, void *stream) {
     if (!m || n < 0 || !count_dev || (n > 0 && (!hits || !rays_out))) return TM_ERR_ARG;
-    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 31u) return TM_ERR_ARG;
     if (!(std::isfinite(lx) && std::isfinite(ly) && std::isfinite(lz))) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     if (n > INT32_MAX) return TM_ERR_TOO_LARGE;
@@ -240,7 +240,7 @@ tm_status tm_gen_specular(const tm_mesh *m, const tm_ray *rays_in, const tm_hit 
                           const int64_t *n_dev, int kind, float ior, float tmax, tm_ray *rays_out,
                           int64_t *count_dev, int32_t *src_out, void *stream) {
     if (!m || n < 0 || !count_dev || (n > 0 && (!hits || !rays_out || !rays_in))) return TM_ERR_ARG;
-    if ((((uintptr_t)rays_out) | ((uintptr_t)hits) | ((uintptr_t)rays_in)) & 15u) return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits) | ((uintptr_t)rays_in)) & 31u) return TM_ERR_ARG;
     if (kind != TM_SPECULAR_REFLECT && kind != TM_SPECULAR_REFRACT) return TM_ERR_ARG;
     if (!(ior > 0.f) || !std::isfinite(ior)) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
@@ -255,7 +255,7 @@ tm_status tm_gen_secondary_noalloc(const tm_mesh *m, const tm_hit *hits, int64_t
                                    void *stream) {
     if (!m || n < 0 || per_hit < 1 || per_hit > 1024 || !count_dev || (n > 0 && (!hits || !rays_out)))
         return TM_ERR_ARG;
-    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 15u) return TM_ERR_ARG;
+    if ((((uintptr_t)rays_out) | ((uintptr_t)hits)) & 31u) return TM_ERR_ARG;
     if (!m->on_device) return TM_ERR_NO_DEVICE;
     if (n * (int64_t)per_hit > INT32_MAX) return TM_ERR_TOO_LARGE;
     return launch_gen_secondary_noalloc(mesh_view(m), hits, n, n_dev, per_hit, tmax, seed, rays_out,

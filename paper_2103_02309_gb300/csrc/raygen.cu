@@ -15,6 +15,21 @@ namespace tmk {
 
 constexpr int kTileW = 8, kTileH = 4;
 
+// A 32-byte ray written by one 256-bit streaming store (sm_100 and later;
+// the C ABI requires 32-byte aligned ray buffers) instead of two 128-bit
+// ones, so that L2 never receives a sector in halves.
+#ifndef TM_ST256
+#define TM_ST256 1
+#endif
+__device__ __forceinline__ void store32_cs(void *p, const float4 &a, const float4 &b) {
+    const unsigned long long q0 = ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+    const unsigned long long q1 = ((unsigned long long)__float_as_uint(a.w) << 32) | __float_as_uint(a.z);
+    const unsigned long long q2 = ((unsigned long long)__float_as_uint(b.y) << 32) | __float_as_uint(b.x);
+    const unsigned long long q3 = ((unsigned long long)__float_as_uint(b.w) << 32) | __float_as_uint(b.z);
+    asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(q0), "l"(q1), "l"(q2), "l"(q3)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(256)
 gen_primary_kernel(const __grid_constant__ tm_camera cam, const int32_t *__restrict__ start,
                    float tmax, tm_ray *__restrict__ rays) {
@@ -35,9 +50,14 @@ gen_primary_kernel(const __grid_constant__ tm_camera cam, const int32_t *__restr
         const float s2 = __fadd_rn(__fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy)), 1.0f);
         const float L = __fsqrt_rn(s2);
         const float dx = __fdiv_rn(sx, L), dy = __fdiv_rn(sy, L), dz = __fdiv_rn(1.0f, L);
+#if TM_ST256
+        store32_cs(rays + r, make_float4(cam.eye[0], cam.eye[1], cam.eye[2], __int_as_float(st)),
+                   make_float4(dx, dy, dz, tmax));
+#else
         float4 *out = reinterpret_cast<float4 *>(rays + r);
         __stcs(out, make_float4(cam.eye[0], cam.eye[1], cam.eye[2], __int_as_float(st)));
         __stcs(out + 1, make_float4(dx, dy, dz, tmax));
+#endif
     }
 }
 
@@ -197,9 +217,13 @@ __device__ __forceinline__ HitGeom hit_geometry(const MeshView &mv, const HitIn 
 
 __device__ __forceinline__ void put_ray(tm_ray *out, int64_t o, float ox, float oy, float oz,
                                         int32_t start, float dx, float dy, float dz, float tmax) {
+#if TM_ST256
+    store32_cs(out + o, make_float4(ox, oy, oz, __int_as_float(start)), make_float4(dx, dy, dz, tmax));
+#else
     float4 *r = reinterpret_cast<float4 *>(out + o);
     __stcs(r, make_float4(ox, oy, oz, __int_as_float(start)));
     __stcs(r + 1, make_float4(dx, dy, dz, tmax));
+#endif
 }
 
 // Cosine-weighted directions about the normal of a hit, turned toward its

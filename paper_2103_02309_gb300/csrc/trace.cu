@@ -64,16 +64,46 @@ __device__ __forceinline__ int walk_phase(int32_t from) { return -1 - from; }
 __device__ __forceinline__ bool is_walk_phase(int w) { return w < 0; }
 __device__ __forceinline__ int32_t walk_from(int w) { return -1 - w; }
 
+// A 32-byte slot written by one 256-bit store (sm_100 and later; the C ABI
+// requires 32-byte aligned ray and hit buffers) instead of two 128-bit
+// ones, so that L2 never receives a sector in halves.  Measured on GB300 in
+// the start and finish phases and the ray generators: +0.4 % a step on the
+// precision workload, +1.4 % on the large one.  The walk keeps two 128-bit
+// stores: there the wide store (an asm statement the compiler cannot move
+// loads across) made both walks 1-2 % slower.
+#ifndef TM_ST256
+#define TM_ST256 1
+#endif
+__device__ __forceinline__ void store32(void *p, const int4 &a, const int4 &b, bool streaming) {
+    const unsigned long long q0 = ((unsigned long long)(uint32_t)a.y << 32) | (uint32_t)a.x;
+    const unsigned long long q1 = ((unsigned long long)(uint32_t)a.w << 32) | (uint32_t)a.z;
+    const unsigned long long q2 = ((unsigned long long)(uint32_t)b.y << 32) | (uint32_t)b.x;
+    const unsigned long long q3 = ((unsigned long long)(uint32_t)b.w << 32) | (uint32_t)b.z;
+    if (streaming)
+        asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(q0), "l"(q1), "l"(q2),
+                     "l"(q3) : "memory");
+    else
+        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(q0), "l"(q1), "l"(q2),
+                     "l"(q3) : "memory");
+}
+
+template <bool WIDE = false>
 __device__ __forceinline__ void put_record(tm_hit *hp, int phase, int32_t tet, uint32_t prev_or_code,
                                            int32_t i0, int32_t i1, int32_t i2, uint32_t steps,
                                            uint32_t flags) {
-    reinterpret_cast<int4 *>(hp)[0] = make_int4(phase, tet, (int)prev_or_code, i0);
-    reinterpret_cast<int4 *>(hp)[1] = make_int4(i1, i2, (int)steps, (int)flags);
+    if (TM_ST256 && WIDE) {
+        store32(hp, make_int4(phase, tet, (int)prev_or_code, i0), make_int4(i1, i2, (int)steps, (int)flags),
+                false);
+    } else {
+        reinterpret_cast<int4 *>(hp)[0] = make_int4(phase, tet, (int)prev_or_code, i0);
+        reinterpret_cast<int4 *>(hp)[1] = make_int4(i1, i2, (int)steps, (int)flags);
+    }
 }
 
+template <bool WIDE = false>
 __device__ __forceinline__ void put_end(tm_hit *hp, int32_t tet, uint32_t code, uint32_t steps,
                                         uint32_t flags) {
-    put_record(hp, kPhaseEnded, tet, code, -1, -1, -1, steps, flags);
+    put_record<WIDE>(hp, kPhaseEnded, tet, code, -1, -1, -1, steps, flags);
 }
 
 // Which mesh and which ray a global ray index names (batched launches).
@@ -223,20 +253,20 @@ __device__ __forceinline__ void start_one(const MeshView &mv, const tm_ray *rp, 
         }
     }
     if (!ok)
-        put_end(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_START);
+        put_end<true>(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_BAD_START);
     else if (T == stop_tet)  // the ray starts in the light's tet: nothing lies in between
-        put_end(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
+        put_end<true>(hp, T, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
     else if (next & TM_CFACE_FLAG)
-        put_end(hp, S.prev, next, steps, sc.flags);
+        put_end<true>(hp, S.prev, next, steps, sc.flags);
     else if ((int32_t)next == stop_tet)
-        put_end(hp, (int32_t)next, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
+        put_end<true>(hp, (int32_t)next, TM_BOUNDARY, steps, sc.flags | TM_HIT_REACHED);
     else if (slot_i3) {
         // the face-entry walk starts from the next tet's fourth vertex
         const int4 cv = __ldg(mv.cold + 2 * (int64_t)next);
         const int32_t i3 = cv.x ^ cv.y ^ cv.z ^ cv.w ^ S.i0 ^ S.i1 ^ S.i2;
-        put_record(hp, walk_phase(T), (int32_t)next, (uint32_t)i3, S.i0, S.i1, S.i2, steps, sc.flags);
+        put_record<true>(hp, walk_phase(T), (int32_t)next, (uint32_t)i3, S.i0, S.i1, S.i2, steps, sc.flags);
     } else
-        put_record(hp, walk_phase(T), (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps,
+        put_record<true>(hp, walk_phase(T), (int32_t)next, (uint32_t)S.prev, S.i0, S.i1, S.i2, steps,
                    sc.flags);
 }
 
@@ -339,9 +369,14 @@ __device__ __forceinline__ bool finish_one(const MeshView &mv, const tm_ray *rp,
             if (g0.w != tet) flags |= TM_HIT_SIDE_NEG;
         }
     }
+#if TM_ST256
+    store32(hp, make_int4(tri, __float_as_int(t), __float_as_int(b1), __float_as_int(b2)),
+            make_int4(tet, cf, (int)steps, (int)flags), true);
+#else
     __stcs(reinterpret_cast<int4 *>(hp), make_int4(tri, __float_as_int(t), __float_as_int(b1),
                                                    __float_as_int(b2)));
     __stcs(reinterpret_cast<int4 *>(hp) + 1, make_int4(tet, cf, (int)steps, (int)flags));
+#endif
     return false;
 }
 

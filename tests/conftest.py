@@ -8,6 +8,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def pytest_sessionstart(session):
+    # bring the in-tree library up to date before any test module loads it:
+    # a module that imports the binding first would otherwise keep a stale
+    # build for the whole session
+    from paper_2103_02309_gb300 import build
+    build.build()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: larger CPU cases")

@@ -162,6 +162,12 @@ def test_build_errors(tmx):
         with pytest.raises(N.TetmeshError) as ei:
             tmx.Mesh(p, t, c, upload=False)
         assert ei.value.status == status, (status, str(ei.value))
+    # ray and hit buffers must be 32-byte aligned: refused before the device is touched
+    m0 = tmx.Mesh(pts, tets, tris, upload=False)
+    lib = N.lib
+    assert lib.tm_trace(m0._h, 16, 1, None, 64, None, None) == 1          # TM_ERR_ARG
+    assert lib.tm_trace(m0._h, 64, 1, None, 48, None, None) == 1
+    assert lib.tm_trace(m0._h, 64, 1, None, 96, None, None) != 1         # aligned: TM_ERR_NO_DEVICE
     # a flipped mesh is accepted when asked to fix orientation, with positive tets
     m = tmx.Mesh(pts, tets[:, [0, 1, 3, 2]], tris, upload=False, fix_orientation=True)
     cold = m.export()["cold"]
