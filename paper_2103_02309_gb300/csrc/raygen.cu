@@ -30,21 +30,27 @@ __device__ __forceinline__ void store32_cs(void *p, const float4 &a, const float
                  : "memory");
 }
 
+// One warp per 8x4 pixel tile (lane -> column lane % 8, row lane / 8), a
+// block's eight warps along a tile row, blockIdx.y the tile row: the ray
+// index follows from the pixel with shifts and products only.  Tile rows
+// hold kTileH full rows (the last may be shorter); within a row, tiles are
+// kTileW wide (the last may be narrower), and a tile's rays are row-major.
 __global__ void __launch_bounds__(256)
 gen_primary_kernel(const __grid_constant__ tm_camera cam, const int32_t *__restrict__ start,
                    float tmax, tm_ray *__restrict__ rays) {
-    const int64_t W = cam.width, H = cam.height, n = W * H;
+    const int64_t W = cam.width, H = cam.height;
+    const int64_t tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
     const int32_t st = *start;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        // ray index -> pixel (tile rows of kTileH full rows, the last may be shorter)
-        const int64_t ty = r / (kTileH * W);
-        const int64_t rem = r - ty * kTileH * W;
+    const int lane = threadIdx.x & 31;
+    const int64_t tx = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tx >= tiles_x) return;
+    const int64_t lx = lane % kTileW, ly = lane / kTileW;
+    const int64_t tw = min((int64_t)kTileW, W - tx * kTileW);
+    for (int64_t ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
         const int64_t th = min((int64_t)kTileH, H - ty * kTileH);
-        const int64_t tx = rem / (kTileW * th);
-        const int64_t rem2 = rem - tx * kTileW * th;
-        const int64_t tw = min((int64_t)kTileW, W - tx * kTileW);
-        const int64_t px = tx * kTileW + rem2 % tw, py = ty * kTileH + rem2 / tw;
+        if (lx >= tw || ly >= th) continue;
+        const int64_t px = tx * kTileW + lx, py = ty * kTileH + ly;
+        const int64_t r = ty * kTileH * W + tx * kTileW * th + ly * tw + lx;
         const float sx = __fmul_rn(__fsub_rn(__fmul_rn(__fadd_rn((float)px, 0.5f), cam.kx), 1.0f), cam.tx);
         const float sy = __fmul_rn(__fsub_rn(1.0f, __fmul_rn(__fadd_rn((float)py, 0.5f), cam.ky)), cam.ty);
         const float s2 = __fadd_rn(__fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy)), 1.0f);
@@ -501,9 +507,12 @@ tm_status launch_gen_primary(const tm_camera *cam, const int32_t *start, float t
                              cudaStream_t s) {
     const int64_t n = (int64_t)cam->width * cam->height;
     if (n == 0) return TM_OK;
-    int64_t grid = (n + 255) / 256;
-    if (grid > 65535 * 8) grid = 65535 * 8;
-    tmk::gen_primary_kernel<<<(int)grid, 256, 0, s>>>(*cam, start, tmax, rays);
+    const int64_t tiles_x = ((int64_t)cam->width + tmk::kTileW - 1) / tmk::kTileW;
+    const int64_t tiles_y = ((int64_t)cam->height + tmk::kTileH - 1) / tmk::kTileH;
+    const int64_t gx = (tiles_x + 7) / 8;                    // eight tiles (warps) a block
+    if (gx > INT32_MAX) return TM_ERR_TOO_LARGE;
+    const dim3 grid((unsigned)gx, (unsigned)(tiles_y < 65535 ? tiles_y : 65535));
+    tmk::gen_primary_kernel<<<grid, 256, 0, s>>>(*cam, start, tmax, rays);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         tm_set_error("gen_primary_kernel launch", e);
