@@ -886,7 +886,7 @@ def cpu_baseline(workload, s, W, budget_s=20.0, om=None):
                            f"rays, Moller-Trumbore against all {s.n_tris} triangles; {tb} rays "
                            f"in {db:.2f} s"}
     return {"value": sig4(traced / dt / 1e6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"every {stride}th pixel of the {s.camera.width}x{s.camera.height} image "
+            "sample": f"{'every' if stride == 1 else f'every {stride}th'} pixel of the {s.camera.width}x{s.camera.height} image "
                       f"({len(sel)} primary rays) + their {W['kind']} rays"
                       + (f", {passes} passes" if passes > 1 else "")
                       + f"; {traced} rays in {dt:.1f} s ("
