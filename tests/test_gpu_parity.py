@@ -130,7 +130,7 @@ def test_tiny_camera_all_rays(tmx, tiny, mode):
     assert np.array_equal(g["cface"][hit], w["tri"][hit])
 
 
-@pytest.mark.parametrize("w,h", [(64, 64), (37, 13), (8, 4), (1, 1)])
+@pytest.mark.parametrize("w,h", [(64, 64), (37, 13), (8, 4), (1, 1), (123, 77), (2050, 5), (9, 300)])
 def test_gen_primary_bit_exact(tmx, tiny, w, h):
     cam = sg.Camera(tiny.s.camera.eye, 60.0, w, h)
     o, d = sg.camera_rays(cam)
