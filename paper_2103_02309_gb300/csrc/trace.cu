@@ -394,11 +394,13 @@ __device__ __forceinline__ bool finish_at(const MeshView &mv0, const tm_ray *ray
 
 constexpr int kFinishBlock = 256;
 // Start and finish grids: at most this many 256-thread blocks per SM
-// (grid-stride beyond).  32 lets the guard-mode finish give each block one
-// 1024-ray chunk on the precision workload; measured 0.5 % faster per step
-// than 16, and 256 slows the start phase.
+// (grid-stride beyond).  24 is a whole number of waves for both phases
+// (three start blocks and four finish blocks fit an SM at once): measured
+// 0.3 % faster per step than 32 on the precision workload (the start
+// phases 4 % shorter), equal on the large one; 16 was 0.5 % slower than 32
+// and 256 slows the start phase.
 #ifndef TM_PHASE_CTAS_PER_SM
-#define TM_PHASE_CTAS_PER_SM 32
+#define TM_PHASE_CTAS_PER_SM 24
 #endif
 #ifndef TM_FINISH_RAYS_PER_THREAD
 #define TM_FINISH_RAYS_PER_THREAD 4
