@@ -83,7 +83,7 @@ def test_cpu_baseline_sizes_its_sample_and_times_brute_force():
     s = sg.make_config("tiny")
     cb = bench.cpu_baseline("tiny", s, dict(bench.WORKLOADS["tiny"]), budget_s=0.5)
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0
-    assert "every 1th pixel" in cb["sample"]          # the whole 64x64 frame fits the budget
+    assert "every pixel" in cb["sample"]              # the whole 64x64 frame fits the budget
     assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
     assert cb["bruteforce"]["value"] > 0 and "192 triangles" in cb["bruteforce"]["sample"]
 
