@@ -394,13 +394,16 @@ __device__ __forceinline__ bool finish_at(const MeshView &mv0, const tm_ray *ray
 
 constexpr int kFinishBlock = 256;
 // Start and finish grids: at most this many 256-thread blocks per SM
-// (grid-stride beyond).  24 is a whole number of waves for both phases
-// (three start blocks and four finish blocks fit an SM at once): measured
-// 0.3 % faster per step than 32 on the precision workload (the start
-// phases 4 % shorter), equal on the large one; 16 was 0.5 % slower than 32
-// and 256 slows the start phase.
-#ifndef TM_PHASE_CTAS_PER_SM
-#define TM_PHASE_CTAS_PER_SM 24
+// (grid-stride beyond), each a whole number of waves (three start blocks
+// and four finish blocks fit an SM at once).  Measured on the precision
+// workload: the start phases 4-6 % shorter at 24 than at 32; the finish
+// phases 5 % longer at 24 than at 32, where each block takes one chunk of
+// 1024 rays; 16 was 0.5 % slower a step than 32, and 256 slows the start.
+#ifndef TM_START_CTAS_PER_SM
+#define TM_START_CTAS_PER_SM 24
+#endif
+#ifndef TM_FINISH_CTAS_PER_SM
+#define TM_FINISH_CTAS_PER_SM 32
 #endif
 #ifndef TM_FINISH_RAYS_PER_THREAD
 #define TM_FINISH_RAYS_PER_THREAD 4
@@ -1189,9 +1192,9 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     P.stop_tet = MULTI ? nullptr : W.stop_tet;
     P.slot_i3 = FMT == TM_FORMAT_FACE || FMT == TM_FORMAT_FACE16;
     const int sms = sm_count_cached();
-    int64_t g = (W.n_cap + 255) / 256;
-    const int64_t gmax = (int64_t)sms * TM_PHASE_CTAS_PER_SM;
-    if (g > gmax) g = gmax;
+    const int64_t g1 = (W.n_cap + 255) / 256;
+    const int64_t g = std::min<int64_t>(g1, (int64_t)sms * TM_START_CTAS_PER_SM);
+    const int64_t gmax = (int64_t)sms * TM_FINISH_CTAS_PER_SM;
     if (ev && ev[0]) cudaEventRecord(ev[0], s);
     start_kernel<MODE, MULTI><<<(int)g, 256, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
     if (ev && ev[1]) cudaEventRecord(ev[1], s);
@@ -1199,7 +1202,7 @@ cudaError_t launch_phases(const MeshView &mv, const tm_ray *rays, tm_hit *hits, 
     walk_kernel<MODE, FMT, BOUNDED, MULTI><<<walk_grid, block, smem, s>>>(mv, rays, hits, descs,
                                                                            n_meshes, W);
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
-    int64_t gf = g;
+    int64_t gf = std::min<int64_t>(g1, gmax);
     if (MODE == FP32G) gf = std::min<int64_t>((W.n_cap + kFinishChunk - 1) / kFinishChunk, gmax);
     finish_kernel<MODE, MULTI><<<(int)gf, kFinishBlock, 0, s>>>(mv, rays, hits, descs, n_meshes, P);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
