@@ -444,6 +444,43 @@ def test_precision_full_frame(tmx, precision, mode):
     print(mode, "primary", st, "device bounce", st2, "oracle bounce", st3)
 
 
+@pytest.mark.parametrize("kind", ["shadow", "reflect", "refract"])
+def test_precision_full_frame_other_secondary_rays(tmx, precision, kind):
+    """The bench's whole frame with its other secondary rays: every shadow
+    ray toward a point light (the walk stopping at the light's tet), every
+    mirror ray and every refraction ray the device generates from its own
+    hits, traced on the device and, every one of them, by the oracle from its
+    restart face (Sec. 6)."""
+    c = precision
+    cam = c.s.camera
+    start = dev(np.array([c.cam_internal], np.int32))
+    rays = tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, cam.width, cam.height), start)
+    hits = c.mesh.trace(rays)
+    if kind == "shadow":
+        light = (0.3, 0.75, 0.05)
+        lt = c.mesh.locate(torch.tensor([light], dtype=torch.float32, device="cuda"))
+        r2, cnt, _ = c.mesh.gen_shadow(hits, light)
+        h2 = c.mesh.trace_shadow(r2, lt, n_dev=cnt)
+    else:
+        r2, cnt, _ = c.mesh.gen_specular(rays, hits, kind, 1.5)
+        h2 = c.mesh.trace(r2, n_dev=cnt)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    assert k > 0.9 * cam.width * cam.height
+    rb = r2[:k].cpu().numpy()
+    g2 = tmx.unpack_hits(h2[:k])
+    entry = -1 - rb.view(np.int32)[:, 3]
+    w2 = c.oracle_trace(rb[:, 0:3], rb[:, 4:7], rb[:, 7], -1, entry)
+    st = compare(c.s.points, c.s.tris, g2, w2)
+    if kind == "shadow":
+        reached = (g2["flags"] & tmx.HIT_REACHED) != 0
+        assert not reached[g2["tri"] >= 0].any()
+        lit = (w2["tri"] < 0) & (g2["tri"] < 0)
+        assert lit.sum() > 1000 and (w2["tri"] >= 0).sum() > 1000
+        assert reached[lit].mean() > 0.999
+    print(kind, st)
+
+
 @pytest.mark.parametrize("faces", [False, True])
 def test_batch_matches_single_launches(tmx, faces):
     """One persistent launch over uneven meshes equals one launch per mesh, for
