@@ -110,3 +110,33 @@ def test_large_full_size_sampled(tmx, large, mode):
     wp = L.ts.bruteforce(rp[:, 0:3], rp[:, 4:7], rp[:, 7], exclude=ep >> 1)
     st3 = compare(L.s.points, L.s.tris, gp, wp)
     print(mode, "primary", st, "ao", st2, "device ao", st3)
+
+
+def test_large_scene_at_128_cells_every_ray(tmx):
+    """The large workload's scene reduced to 128^3 cells (12.6 M tets, a size
+    whose adjacency the oracle builds): every camera ray of the 1024 x 1024
+    frame and every one of the 8.39 M occlusion rays the device generates
+    from its hits, walked as the benchmark walks them (bounded walks that
+    stop at t_max), against the oracle's walk from each ray's start tet or
+    restart face."""
+    from tests.test_gpu_parity import camera_case
+    c = camera_case(tmx, "large", n_override=128)
+    cam = c.s.camera
+    assert cam.width * cam.height == 1024 * 1024
+    start = dev(np.array([c.cam_internal], np.int32))
+    rays = tmx.gen_primary(tmx.make_camera(cam.eye, cam.fov_deg, cam.width, cam.height), start)
+    hits = c.mesh.trace(rays)
+    r2, cnt, _ = c.mesh.gen_secondary(hits, AO_PER_HIT, AO_TMAX, seed=AO_SEED)
+    h2 = c.mesh.trace(r2, n_dev=cnt, tmax_early_exit=True)
+    torch.cuda.synchronize()
+    o, d = sg.camera_rays(cam)
+    g = tmx.unpack_hits(hits)
+    st = compare(c.s.points, c.s.tris, g, c.oracle_trace(o, d, np.inf, c.cam_in[0]))
+    k = int(cnt.item())
+    assert k == AO_PER_HIT * int((g["tri"] >= 0).sum())
+    rb = r2[:k].cpu().numpy()
+    g2 = tmx.unpack_hits(h2[:k])
+    entry = -1 - rb.view(np.int32)[:, 3]
+    st2 = compare(c.s.points, c.s.tris, g2, c.oracle_trace(rb[:, 0:3], rb[:, 4:7], rb[:, 7], -1, entry))
+    assert st2["hits"] > 1000 and st2["n"] - st2["hits"] > 1000     # occluded and open rays
+    print("primary", st, "occlusion", st2)
