@@ -333,9 +333,11 @@ tm_status tm_gen_primary(const tm_camera *cam, const int32_t *start_dev, float t
  * DEVICE rays_out (capacity n*per_hit) in 8 groups by the length of the
  * longest walk the hit's first ray can make (to the mesh's bounding box, or
  * to tmax), longest first, so that a walk over them takes its long rays
- * early and ends with a shorter tail; within a group the hits keep their
- * order, and the per_hit rays of one hit are consecutive.  The order does
- * not depend on scheduling.  The count is written to DEVICE *count_dev
+ * early and ends with a shorter tail.  Within a group, hits go by block of
+ * 1024 consecutive hits, then by the octant of their first ray's direction
+ * (bit 0: dx < 0, bit 1: dy < 0, bit 2: dz < 0), then in hit order, and the
+ * per_hit rays of one hit are consecutive.  The order does not depend on
+ * scheduling.  The count is written to DEVICE *count_dev
  * (int64), and src_out (DEVICE int32, may be NULL) gets the index i of each
  * ray's hit.  hits may hold n_dev (DEVICE int64, may be
  * NULL) valid entries instead of n.  A hit whose cface is not a constrained

@@ -5,7 +5,8 @@
 // light.  Rays from hits are compacted with a three-pass scan (count per
 // block, scan of the block counts, emit), so the output order does not
 // depend on scheduling: shadow and specular rays in hit order, diffuse and
-// occlusion rays by length bucket, in hit order within a bucket.
+// occlusion rays by length bucket; within a bucket, by block of 1024 hits,
+// then by the octant of the hit's first direction, then in hit order.
 #include <mutex>
 #include <string>
 
@@ -386,24 +387,76 @@ count_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__rest
     }
 }
 
+// Inside a block's share of a length group, hits go by the octant of their
+// first ray's direction, then in hit order: keys b * 8 + octant, a warp's
+// lanes of one key found with __match_any_sync, and one exclusive scan per
+// group over (octant, j, warp).  Rays that leave a neighbourhood in one
+// octant walk it together: on GB300 the precision workload's bounce walk
+// took 1.5 % less time (0.4 % a step, the emit pass's extra work included).
+#ifndef TM_EMIT_OCTANTS
+#define TM_EMIT_OCTANTS 1
+#endif
 __global__ void __launch_bounds__(kEmitThreads, 2)
 emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restrict__ hits,
                       int64_t n, const int64_t *n_dev, const int64_t *__restrict__ offsets,
                       int per_hit, float tmax, uint64_t seed, tm_ray *__restrict__ out,
                       int32_t *__restrict__ src) {
     constexpr int PER = kScanBlock / kEmitThreads;
-    __shared__ int wc[PER][kLengthBuckets][kEmitThreads / 32];
+    constexpr int kWarps = kEmitThreads / 32;
+    static_assert(PER * kWarps == 32, "one count a lane");
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     GenHits<PER> g;
     gen_hits<kEmitThreads, PER>(mv, hits, n, n_dev, per_hit, tmax, seed, g);
     unsigned mine[PER];
+    int key[PER];
+#if TM_EMIT_OCTANTS
+    constexpr int kKeys = kLengthBuckets * 8;
+    static_assert(kLengthBuckets * 2 == kWarps && kKeys * PER * kWarps == 256 * kLengthBuckets,
+                  "two warps scan a group's 256 counts, four a thread");
+    __shared__ __align__(16) int wk[kKeys][PER][kWarps];   // key-major: a group's counts are contiguous
+    __shared__ int wtot[kWarps];
+    for (int q = threadIdx.x; q < kKeys * PER * kWarps / 4; q += kEmitThreads)
+        reinterpret_cast<int4 *>(&wk[0][0][0])[q] = make_int4(0, 0, 0, 0);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        key[j] = -1;
+        if (g.b[j] >= 0)
+            key[j] = g.b[j] * 8 + ((g.d0[j].x < 0.f) | ((g.d0[j].y < 0.f) << 1) | ((g.d0[j].z < 0.f) << 2));
+        mine[j] = __match_any_sync(0xffffffffu, key[j]);
+        if (key[j] >= 0 && lane == (unsigned)(__ffs(mine[j]) - 1)) wk[key[j]][j][warp] = __popc(mine[j]);
+    }
+    __syncthreads();
+    {
+        // group b = warp / 2: its 256 counts in (octant, j, warp) order, four
+        // a thread; exclusive prefix left in place
+        const int b = (int)(warp >> 1), t = (int)(((warp & 1u) << 5) | lane);
+        int4 *cell = reinterpret_cast<int4 *>(&wk[b * 8][0][0]) + t;
+        const int4 v = *cell;
+        const int tot = v.x + v.y + v.z + v.w;
+        int x = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        if (lane == 31) wtot[warp] = x;
+        __syncthreads();
+        int e = ((warp & 1u) ? wtot[warp - 1] : 0) + x - tot;
+        int4 r;
+        r.x = e; e += v.x;
+        r.y = e; e += v.y;
+        r.z = e; e += v.z;
+        r.w = e;
+        *cell = r;
+    }
+    __syncthreads();
+#else
+    __shared__ int wc[PER][kLengthBuckets][kEmitThreads / 32];
     gen_ballots<kEmitThreads, PER>(g.b, wc, mine);
     __syncthreads();
-    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     // The block's hits of bucket b before (j, warp), in its hit order (j
     // first, then warp): warp b scans bucket b's PER x warps counts, one a
     // lane, and leaves the exclusive prefix in place.
-    constexpr int kWarps = kEmitThreads / 32;
-    static_assert(PER * kWarps == 32, "one count a lane");
     if (warp < (unsigned)kLengthBuckets) {
         int *cell = &wc[lane / kWarps][warp][lane % kWarps];
         const int v = *cell;
@@ -415,14 +468,20 @@ emit_secondary_kernel(const __grid_constant__ MeshView mv, const tm_hit *__restr
         *cell = x - v;
     }
     __syncthreads();
+#endif
     const int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int b = g.b[j];
         if (b < 0) continue;
-        // the block's earlier hits of bucket b: those before (j, warp), then
-        // the earlier lanes of this warp
+        // the block's earlier hits of bucket b (and octant): those before
+        // (j, warp), then the earlier lanes of this warp
+#if TM_EMIT_OCTANTS
+        const int before = wk[key[j]][j][warp] + __popc(mine[j] & ((1u << lane) - 1u));
+#else
+        (void)key;
         const int before = wc[j][b][warp] + __popc(mine[j] & ((1u << lane) - 1u));
+#endif
         const int64_t pos = offsets[(int64_t)b * gridDim.x + blockIdx.x] + before;
         const int64_t i = base + j * kEmitThreads;
         const BounceFrame &f = g.f[j];

@@ -243,8 +243,9 @@ def host_length_bucket(lo, hi, extent, o, d, tmax, buckets=8):
 
 def test_secondary_rays_grouped_by_length_bucket(tmx, precision):
     """Diffuse bounce rays come out bucket by bucket, the longest possible
-    walks first, hits in order within a bucket; as a set they are the rays
-    of every hit."""
+    walks first; inside a bucket by block of 1024 hits, then by the octant
+    of their direction, then in hit order; as a set they are the rays of
+    every hit."""
     c = precision
     cam = c.s.camera
     start = dev(np.array([c.cam_internal], np.int32))
@@ -262,8 +263,13 @@ def test_secondary_rays_grouped_by_length_bucket(tmx, precision):
     edge = np.abs(ln * 8 - np.round(ln * 8)) < 1e-5               # float ties at a bucket edge
     ok = ~edge
     assert (np.diff(b[ok]) >= 0).all()                          # farthest bucket first
-    for g in np.unique(b[ok]):                                  # hit order inside a bucket
-        assert (np.diff(src[ok][b[ok] == g]) > 0).all()
+    # inside a bucket: by block of 1024 hits, then by the octant of the
+    # direction, then in hit order
+    d2 = r2[:, 4:7]
+    octant = (d2[:, 0] < 0) | ((d2[:, 1] < 0).astype(np.int64) << 1) | ((d2[:, 2] < 0).astype(np.int64) << 2)
+    key = ((src.astype(np.int64) // 1024) * 8 + octant) * (1 << 32) + src.astype(np.int64)
+    for g in np.unique(b[ok]):
+        assert (np.diff(key[ok & (b == g)]) > 0).all()
     assert len(np.unique(b)) >= 4                               # the bounce rays do spread out
 
 
